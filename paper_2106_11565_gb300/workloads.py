@@ -1,0 +1,232 @@
+"""Seeded synthetic workloads and random draws for FLINNG.
+
+This module only draws random numbers and shapes synthetic data. It holds none
+of FLINNG's arithmetic (no hashing of points into tables, no group assignment,
+no decoding): the CUDA library and the CPU oracle both receive what is made here
+as plain arrays.
+
+Random quantities the method itself draws (Alg. 1's permutations, the LSH
+functions' parameters) are produced here once from a seed and passed to both
+sides as data.
+
+Workload shapes follow the paper's datasets (Section 6, Table 1), which are not
+available here; the stand-ins are:
+
+* ``gaussian_mixture``: dense fp32 vectors (cosine / SRP workloads).
+* ``genomic_reads``: reads sampled with substitutions from a random ACGT
+  reference, turned into sets of hashed k-mers (RefSeq / PromethION-shaped).
+* ``url_strings``: token strings from a Zipf vocabulary turned into sets of
+  character 3-grams (URL-shaped).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+U32 = np.uint32
+U64 = np.uint64
+
+CONFIG_SEED_BASE = 0xF11A6
+
+
+def config_seed(config_number: int) -> int:
+    """Seed used for workload ``C<config_number>``."""
+    return CONFIG_SEED_BASE + int(config_number)
+
+
+# --------------------------------------------------------------------------
+# random draws of the method (passed to both sides as data)
+# --------------------------------------------------------------------------
+
+def srp_projections(seed: int, n_proj: int, dim: int) -> np.ndarray:
+    """Gaussian projection rows for sign random projections, (n_proj, dim) fp32."""
+    rng = np.random.default_rng([seed, 1])
+    return rng.standard_normal((n_proj, dim)).astype(np.float32)
+
+
+def doph_params(seed: int, L: int, K: int) -> dict:
+    """Random keys for densified one-permutation MinHash and bucket combining.
+
+    ``doph_a`` is odd, so the 32-bit affine map it defines is a bijection;
+    ``bucket_a`` entries are odd 64-bit multipliers, ``bucket_c`` 64-bit offsets.
+    """
+    rng = np.random.default_rng([seed, 2])
+    a = int(rng.integers(0, 1 << 32, dtype=np.uint64)) | 1
+    b = int(rng.integers(0, 1 << 32, dtype=np.uint64))
+    s = int(rng.integers(0, 1 << 63, dtype=np.uint64)) * 2 + int(rng.integers(0, 2))
+    ba = rng.integers(0, 1 << 63, size=(L, K), dtype=np.uint64) * U64(2) + U64(1)
+    bc = rng.integers(0, 1 << 63, size=(L,), dtype=np.uint64) * U64(2) + \
+        rng.integers(0, 2, size=(L,), dtype=np.uint64)
+    return {"doph_a": a, "doph_b": b, "doph_seed": s & ((1 << 64) - 1),
+            "bucket_a": np.ascontiguousarray(ba, dtype=U64),
+            "bucket_c": np.ascontiguousarray(bc, dtype=U64)}
+
+
+def group_permutations(seed: int, R: int, n: int, batch: int = 0) -> np.ndarray:
+    """R independent uniform permutations of [0, n), shape (R, n) uint32.
+
+    ``batch`` distinguishes the permutations of successive insert batches.
+    """
+    rng = np.random.default_rng([seed, 3, batch])
+    out = np.empty((R, n), dtype=U32)
+    for r in range(R):
+        out[r] = rng.permutation(n).astype(U32)
+    return out
+
+
+# --------------------------------------------------------------------------
+# dense vectors
+# --------------------------------------------------------------------------
+
+def gaussian_mixture(seed: int, n: int, dim: int, n_centers: int,
+                     sigma: float) -> tuple[np.ndarray, np.ndarray]:
+    """Points = center + N(0, sigma^2 I) with centers ~ N(0, I); fp32 (n, dim)."""
+    rng = np.random.default_rng([seed, 10])
+    centers = rng.standard_normal((n_centers, dim))
+    labels = rng.integers(0, n_centers, size=n)
+    pts = centers[labels] + sigma * rng.standard_normal((n, dim))
+    return pts.astype(np.float32), labels
+
+
+def noisy_queries(seed: int, points: np.ndarray, nq: int,
+                  sigma: float) -> tuple[np.ndarray, np.ndarray]:
+    """Queries = a random data point + N(0, sigma^2 I); returns (queries, source ids)."""
+    rng = np.random.default_rng([seed, 11])
+    src = rng.integers(0, points.shape[0], size=nq)
+    q = points[src].astype(np.float64) + sigma * rng.standard_normal((nq, points.shape[1]))
+    return q.astype(np.float32), src
+
+
+# --------------------------------------------------------------------------
+# sets (CSR: uint64 offsets n+1, uint32 elements)
+# --------------------------------------------------------------------------
+
+def csr_from_rows(rows: list[np.ndarray]) -> tuple[np.ndarray, np.ndarray]:
+    off = np.zeros(len(rows) + 1, dtype=U64)
+    if rows:
+        off[1:] = np.cumsum([len(r) for r in rows], dtype=U64)
+    elems = np.concatenate(rows).astype(U32) if rows else np.zeros(0, U32)
+    return off, np.ascontiguousarray(elems)
+
+
+def random_sets(seed: int, n: int, universe: int, min_size: int,
+                max_size: int) -> tuple[np.ndarray, np.ndarray]:
+    """n sets of distinct uint32 elements drawn from [0, universe)."""
+    rng = np.random.default_rng([seed, 20])
+    rows = []
+    for _ in range(n):
+        s = int(rng.integers(min_size, max_size + 1))
+        s = min(s, universe)
+        rows.append(np.sort(rng.choice(universe, size=s, replace=False)).astype(U32))
+    return csr_from_rows(rows)
+
+
+def _dedup_sorted_rows(sorted_rows: np.ndarray) -> list[np.ndarray]:
+    keep = np.ones(sorted_rows.shape, dtype=bool)
+    keep[:, 1:] = sorted_rows[:, 1:] != sorted_rows[:, :-1]
+    return [sorted_rows[i][keep[i]] for i in range(sorted_rows.shape[0])]
+
+
+def genomic_reads(seed: int, ref_len: int, n_reads: int, read_len: int,
+                  n_queries: int, kmer: int = 18, sub_lo: float = 0.01,
+                  sub_hi: float = 0.10) -> dict:
+    """Reads sampled from a uniform random ACGT reference with substitutions.
+
+    Each read is the set of its k-mers: a k-mer is packed 2 bits per base
+    (A=0, C=1, G=2, T=3, first base most significant, forward strand only)
+    and mapped to uint32 by a seeded multiply-shift; each set is deduplicated.
+    Returns CSR sets for the ``n_reads`` indexed reads and the ``n_queries``
+    held-out reads drawn from the same process.
+    """
+    if kmer > 32:
+        raise ValueError("kmer must be <= 32")
+    rng = np.random.default_rng([seed, 30])
+    ref = rng.integers(0, 4, size=ref_len, dtype=np.uint8)
+    key = U64(int(rng.integers(0, 1 << 63, dtype=np.uint64)) * 2 + 1)
+    total = n_reads + n_queries
+    starts = rng.integers(0, ref_len - read_len + 1, size=total)
+    rates = rng.uniform(sub_lo, sub_hi, size=total)
+    nk = read_len - kmer + 1
+    rows: list[np.ndarray] = []
+    chunk = 8192
+    for c0 in range(0, total, chunk):
+        c1 = min(total, c0 + chunk)
+        idx = starts[c0:c1, None] + np.arange(read_len)[None, :]
+        reads = ref[idx].copy()
+        sub = rng.random(reads.shape) < rates[c0:c1, None]
+        shift = rng.integers(1, 4, size=reads.shape, dtype=np.uint8)
+        reads[sub] = (reads[sub] + shift[sub]) & 3
+        codes = np.zeros((c1 - c0, nk), dtype=U64)
+        r64 = reads.astype(U64)
+        for j in range(kmer):
+            codes = (codes << U64(2)) | r64[:, j:j + nk]
+        with np.errstate(over="ignore"):
+            h = ((codes * key) >> U64(32)).astype(U32)
+        h.sort(axis=1)
+        rows.extend(_dedup_sorted_rows(h))
+    off, el = csr_from_rows(rows[:n_reads])
+    qoff, qel = csr_from_rows(rows[n_reads:])
+    return {"off": off, "elems": el, "q_off": qoff, "q_elems": qel,
+            "starts": starts, "rates": rates}
+
+
+_ALPHABET = np.frombuffer(b"abcdefghijklmnopqrstuvwxyz0123456789", dtype=np.uint8)
+
+
+def _gram_sets(strings: list[bytes]) -> list[np.ndarray]:
+    rows = []
+    for s in strings:
+        b = np.frombuffer(s, dtype=np.uint8).astype(U32)
+        if len(b) < 3:
+            rows.append(np.zeros(0, U32))
+            continue
+        g = (b[:-2] << U32(16)) | (b[1:-1] << U32(8)) | b[2:]
+        rows.append(np.unique(g).astype(U32))
+    return rows
+
+
+def url_strings(seed: int, n: int, n_queries: int, vocab: int = 50_000,
+                zipf_s: float = 1.1, median_len: float = 60.0,
+                sigma: float = 0.5, edit_rate: float = 0.05) -> dict:
+    """URL-shaped strings turned into sets of character 3-grams.
+
+    Tokens are random [a-z0-9] words of length 2..12 drawn from a vocabulary
+    by a Zipf(zipf_s) law; a string is tokens joined by '/' until its
+    lognormal target length (median ``median_len``) is reached. A 3-gram is
+    its 3 bytes packed into 24 bits (exact). Queries are copies of random
+    strings with ``edit_rate`` character edits (substitution, insertion or
+    deletion with equal probability).
+    """
+    rng = np.random.default_rng([seed, 40])
+    tok_len = rng.integers(2, 13, size=vocab)
+    tok = [bytes(_ALPHABET[rng.integers(0, len(_ALPHABET), size=int(t))]) for t in tok_len]
+    w = 1.0 / np.arange(1, vocab + 1) ** zipf_s
+    cdf = np.cumsum(w / w.sum())
+    target = np.maximum(3, np.round(rng.lognormal(np.log(median_len), sigma, size=n))).astype(int)
+    strings = []
+    for i in range(n):
+        parts = []
+        ln = 0
+        while ln < target[i]:
+            t = tok[int(np.searchsorted(cdf, rng.random()))]
+            parts.append(t)
+            ln += len(t) + 1
+        strings.append(b"/".join(parts)[: int(target[i])])
+    src = rng.integers(0, n, size=n_queries)
+    queries = []
+    for i in src:
+        s = bytearray(strings[int(i)])
+        n_ed = max(1, int(round(edit_rate * len(s))))
+        for _ in range(n_ed):
+            op = int(rng.integers(0, 3))
+            pos = int(rng.integers(0, max(1, len(s))))
+            ch = int(_ALPHABET[rng.integers(0, len(_ALPHABET))])
+            if op == 0 and len(s) > 0:
+                s[pos] = ch
+            elif op == 1:
+                s.insert(pos, ch)
+            elif len(s) > 1:
+                del s[pos]
+        queries.append(bytes(s))
+    off, el = csr_from_rows(_gram_sets(strings))
+    qoff, qel = csr_from_rows(_gram_sets(queries))
+    return {"off": off, "elems": el, "q_off": qoff, "q_elems": qel, "src": src}
