@@ -1,0 +1,220 @@
+/*
+ * flinng.h - C ABI of the GB300 FLINNG library (libflinng.so).
+ *
+ * FLINNG: Engels, Coleman, Shrivastava, "Practical Near Neighbor Search via
+ * Group Testing" (arXiv 2106.11565). The index answers the randomized
+ * nearest-neighbour problem of Def. 1: given a dataset D and a query y,
+ * report points of D close to y. It is the B x R grid of group tests of
+ * Sec. 4 (Alg. 1 builds it, Alg. 2 / Alg. 3 query it), each test a
+ * distance-sensitive Bloom filter (Sec. 3.3) stored as a reverse index
+ * (Sec. 5).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ *  - Return value: FLINNG_OK (0) or one of the FLINNG_ERR_* codes below;
+ *    flinng_last_error() then gives a message (thread-local, valid until the
+ *    next call on the same thread). A failed call leaves the index as it was
+ *    unless the message says otherwise.
+ *  - Memory: the index owns all device memory it allocates (at create time,
+ *    sized by flinng_config.capacity, plus a workspace that grows with the
+ *    largest batch seen). The caller owns every input and output buffer.
+ *    No caller pointer is kept after a call returns.
+ *  - on_device: 1 means every caller buffer of the call is CUDA device memory
+ *    of the current device; the call is then asynchronous on the index's
+ *    stream (synchronise that stream before reading outputs or freeing
+ *    inputs). 0 means every caller buffer is host memory; the call copies
+ *    in, computes, copies out and returns after the stream is idle.
+ *  - Point ids are insertion order: the first build gives ids 0..n-1, each
+ *    insert continues the numbering.
+ *  - Cell ids are r * B + b for repetition r and group b; they are 16-bit
+ *    (B * R <= 65536, the paper's "BR < 2^16", Sec. 5 and appendix).
+ */
+#ifndef FLINNG_H
+#define FLINNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FLINNG_OK 0
+#define FLINNG_ERR_INVALID_ARG 1 /* bad size, pointer, config or permutation */
+#define FLINNG_ERR_OOM 2         /* device allocation failed */
+#define FLINNG_ERR_CAPACITY 3    /* insert would exceed flinng_config.capacity */
+#define FLINNG_ERR_CUDA 4        /* a CUDA call failed (message has the CUDA error) */
+#define FLINNG_ERR_TIMEOUT 5     /* a bounded device-side wait gave up */
+
+/* similarity / LSH family */
+#define FLINNG_COSINE_SRP 0      /* dense fp32 vectors, sign random projections */
+#define FLINNG_JACCARD_DOPH 1    /* sets of uint32, densified one-permutation MinHash */
+
+/* arithmetic of the SRP projection (cosine only) */
+#define FLINNG_PREC_FP32 0
+
+typedef struct flinng_config {
+    uint32_t metric;        /* FLINNG_COSINE_SRP or FLINNG_JACCARD_DOPH */
+    uint32_t dim;           /* cosine: vector length d (1..65536); ignored for sets */
+    uint32_t R;             /* repetitions, 1..8 (Sec. 3.1) */
+    uint32_t B;             /* groups per repetition, B * R <= 65536 (Sec. 3.1) */
+    uint32_t L;             /* hash tables = Bloom-filter arrays, 1..255 (paper: m) */
+    uint32_t K;             /* hashes concatenated per table (paper: L, Sec. 3.2);
+                               SRP: 1..30 (it is also W) */
+    uint32_t range_bits;    /* W: buckets per table = 2^W; SRP requires W == K;
+                               1..30 with L * 2^W < 2^31 */
+    uint32_t min_threshold; /* t_min >= 1: cells with fewer collisions never test
+                               positive (Sec. 5 threshold t, relaxed by Alg. 3) */
+    uint32_t precision;     /* FLINNG_PREC_FP32 */
+    uint32_t reserved;
+    uint64_t capacity;      /* maximum number of points, inserts included;
+                               L * R * capacity < 2^32 */
+} flinng_config;
+
+/* Hash parameters: the LSH functions shared by all filters (Sec. 5), drawn by
+ * the caller from its seed and passed as data. Host pointers, copied at
+ * create time. */
+typedef struct flinng_params {
+    const float *srp_w;         /* cosine: (L*K) x dim row-major fp32 projection
+                                   rows; row l*K + j gives bit j of table l */
+    uint32_t doph_a;            /* Jaccard: pi(e) = doph_a * e + doph_b mod 2^32; odd */
+    uint32_t doph_b;
+    uint64_t doph_seed;         /* Jaccard: seed of the densification choices */
+    const uint64_t *bucket_a;   /* Jaccard: L x K odd multipliers */
+    const uint64_t *bucket_c;   /* Jaccard: L offsets */
+} flinng_params;
+
+/* A batch of points or queries. */
+typedef struct flinng_points {
+    const float *x;             /* cosine: n x dim fp32, row stride ld floats */
+    uint64_t ld;                /* cosine: row stride (>= dim) */
+    const uint64_t *off;        /* Jaccard: n + 1 offsets into elems (off[0] = 0,
+                                   non-decreasing) */
+    const uint32_t *elems;      /* Jaccard: set elements; duplicates allowed */
+} flinng_points;
+
+typedef struct flinng_index flinng_index;
+
+/*
+ * Create an empty index on the current CUDA device.
+ * Allocates the index's device memory for cfg->capacity points.
+ * stream: a cudaStream_t, or NULL for the legacy default stream.
+ * Errors: INVALID_ARG (config out of range, missing params), OOM, CUDA.
+ */
+int flinng_create(const flinng_config *cfg, const flinng_params *params,
+                  void *stream, flinng_index **out);
+
+/*
+ * Build the index from scratch over n points (Alg. 1 then Sec. 5): discards
+ * the previous contents, hashes every point with the L shared LSH functions,
+ * assigns point perm[r][i] to cell (r, i mod B) for each repetition r, and
+ * writes the reverse index (per table: bucket -> sorted list of distinct cell
+ * ids) in one pass.
+ * perm: R x n uint32, row r a permutation of [0, n) (Alg. 1's random
+ * permutation pi, drawn by the caller).
+ * Errors: INVALID_ARG (a row of perm is not a permutation, n = 0 is allowed),
+ * CAPACITY (n > capacity), CUDA.
+ */
+int flinng_build(flinng_index *idx, const flinng_points *pts, uint64_t n,
+                 const uint32_t *perm, int on_device);
+
+/*
+ * Add n points with ids size .. size+n-1. Alg. 1 applied to the batch with
+ * positions continuing after the current size: position i of row r of perm
+ * goes to cell (r, (size + i) mod B). The reverse index becomes that of the
+ * union.
+ * Errors: as flinng_build; CAPACITY leaves the index unchanged.
+ */
+int flinng_insert(flinng_index *idx, const flinng_points *pts, uint64_t n,
+                  const uint32_t *perm, int on_device);
+
+/*
+ * Batched query (Sec. 5 with Alg. 3): hash each query once, count per cell
+ * the tables whose bucket list holds the cell, and return the points in
+ * Alg. 3's order - cells by count descending (ties: cell id ascending),
+ * points as their last cell is reached, by id within a cell - keeping
+ * only points whose R cells all have count >= min_threshold.
+ * k: per-query result counts (nq entries, each <= k_max), or NULL for k_max
+ * for every query. k_max <= 1024.
+ * out_ids: nq x k_max point ids, padded with 0xFFFFFFFF.
+ * out_scores: nq x k_max, the score of each returned point (the least count
+ * among its R cells), padded with 0; may be NULL.
+ * Errors: INVALID_ARG (k > k_max, k_max > 1024, null outputs), CUDA.
+ */
+int flinng_query(flinng_index *idx, const flinng_points *q, uint32_t nq,
+                 const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
+                 uint8_t *out_scores, int on_device);
+
+/* Destroy the index and free its device memory. NULL is a no-op. */
+int flinng_destroy(flinng_index *idx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *flinng_last_error(void);
+
+/* Number of points in the index. */
+uint64_t flinng_size(const flinng_index *idx);
+
+/* Device bytes held by the index (index arrays, scratch, workspace). */
+uint64_t flinng_device_bytes(const flinng_index *idx);
+
+/* Set the stream used by subsequent calls (cudaStream_t or NULL). */
+int flinng_set_stream(flinng_index *idx, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Stage entry points, for parity checks of each step against a reference */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Hash n points with the index's LSH functions (Sec. 3.2 concatenation,
+ * Sec. 5 shared functions).
+ * out_buckets: n x L uint32 bucket per table (SRP: the K sign bits, bit j =
+ *   (projection l*K + j > 0); Jaccard: the W-bit combination of the K MinHash
+ *   values of table l).
+ * out_values: Jaccard only, n x (L*K) uint32 MinHash values, or NULL.
+ * out_proj: cosine only, n x (L*K) fp32 projections as computed before the
+ *   sign decision, or NULL.
+ */
+int flinng_hash(flinng_index *idx, const flinng_points *pts, uint64_t n,
+                uint32_t *out_buckets, uint32_t *out_values, float *out_proj,
+                int on_device);
+
+/*
+ * Query from precomputed buckets (nq x L), skipping the hash step.
+ * Same outputs as flinng_query.
+ */
+int flinng_query_buckets(flinng_index *idx, const uint32_t *qbuckets,
+                         uint32_t nq, const uint32_t *k, uint32_t k_max,
+                         uint32_t *out_ids, uint8_t *out_scores,
+                         int on_device);
+
+/*
+ * Per-cell collision counts of nq queries given their buckets (Sec. 5):
+ * out_counts nq x (B*R) uint8.
+ */
+int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq,
+                  uint8_t *out_counts, int on_device);
+
+/*
+ * Copy the index out to HOST buffers (synchronous).
+ * off: L * 2^W + 1 uint32 CSR offsets; cells: the cell lists (cells_cap
+ * entries available; *n_cells receives the count); gid: size x R uint16
+ * cell of each point per repetition (group b, not r*B+b). Any may be NULL.
+ * Errors: CAPACITY if cells_cap is too small (nothing written to cells).
+ */
+int flinng_export(flinng_index *idx, uint32_t *off, uint16_t *cells,
+                  uint64_t cells_cap, uint64_t *n_cells, uint16_t *gid);
+
+/* Counters of the last hash call: SRP projections re-checked in fp64 and
+ * those that needed the exact accumulator. */
+int flinng_hash_stats(const flinng_index *idx, uint64_t *n_recheck,
+                      uint64_t *n_exact);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * indices, all threads); memset/memcpy operations are not counted. */
+uint64_t flinng_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLINNG_H */

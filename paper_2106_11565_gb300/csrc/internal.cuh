@@ -1,0 +1,136 @@
+// Internal declarations of the FLINNG CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "flinng.h"
+
+namespace flinng {
+
+constexpr uint32_t kEmpty32 = 0xFFFFFFFFu;
+constexpr uint64_t kKeyNone = ~0ull;
+constexpr uint32_t kMaxKMax = 1024;
+constexpr uint32_t kDophMaxAttempts = 4096;
+
+// Error plumbing: every internal step returns an int status and leaves a
+// message in the thread-local buffer.
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what);
+
+#define FL_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::flinng::cuda_error(e_, #call);  \
+    } while (0)
+
+#define FL_TRY(call)                      \
+    do {                                  \
+        int rc_ = (call);                 \
+        if (rc_ != FLINNG_OK) return rc_; \
+    } while (0)
+
+// Grow-only device scratch region.
+struct Workspace {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// Bump allocator over a workspace, 256-byte aligned slices.
+struct Carver {
+    char *base;
+    size_t cap, used = 0;
+    Carver(void *p, size_t c) : base((char *)p), cap(c) {}
+    template <class T>
+    T *take(size_t n) {
+        size_t a = (used + 255) & ~size_t(255);
+        used = a + n * sizeof(T);
+        return (T *)(base + a);
+    }
+};
+
+template <class T>
+inline size_t carve_bytes(size_t n) { return ((n * sizeof(T) + 255) & ~size_t(255)) + 256; }
+
+}  // namespace flinng
+
+struct flinng_index {
+    flinng_config cfg;
+    cudaStream_t stream;
+    int device;
+
+    // hash parameters (device copies)
+    float *srp_w;          // P x dim
+    uint64_t *bucket_a;    // L x K
+    uint64_t *bucket_c;    // L
+    uint32_t doph_a, doph_b;
+    uint64_t doph_seed;
+    float srp_margin_gamma;   // 2 * gamma_d in fp32, rounded up
+    double srp_gamma64;       // 2 * gamma_d for the fp64 recheck
+
+    // shape
+    uint32_t P;            // L * K projections / MinHash values per point
+    uint32_t rp;           // gid row stride (R rounded up to 1, 2, 4 or 8)
+    uint32_t BR;
+    uint64_t nslot;        // L << W
+    uint64_t entries_cap;  // L * R * capacity
+
+    // index state
+    uint64_t n_points;
+    uint64_t n_cells;
+    uint16_t *gid;         // capacity x rp
+    uint32_t *moff;        // BR + 1: members of cell c are mem[moff[c] .. moff[c+1])
+    uint32_t *mem;         // R * capacity point ids
+    uint32_t *off;         // nslot + 1
+    uint16_t *cells;       // entries_cap
+    uint16_t *cells_tmp;   // entries_cap (build scratch)
+    uint32_t *slot_a;      // nslot + 1 (build scratch)
+    uint32_t *slot_b;      // nslot + 1 (build scratch)
+    uint32_t *cell_cnt;    // BR + 1 (build scratch)
+    uint32_t *flag;        // device status word
+    uint32_t *h_flag;      // pinned host copy
+    unsigned long long *stats;   // [recheck, exact]
+    uint64_t last_recheck, last_exact;
+
+    flinng::Workspace ws;
+    uint64_t device_bytes;
+};
+
+namespace flinng {
+
+int ws_reserve(flinng_index *ix, size_t bytes);
+
+// Process-wide count of kernel launches made by the library.
+void count_launch(unsigned n = 1);
+
+// ---- scan.cu
+size_t scan_workspace_bytes(size_t n);
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total.
+int scan_exclusive(const uint32_t *in, uint32_t *out, size_t n, void *ws,
+                   cudaStream_t st);
+
+// ---- hash.cu
+// SRP: buckets n x L; proj (optional) n x P; rows of x with stride ld.
+size_t srp_workspace_bytes(const flinng_index *ix, uint64_t n);
+int srp_hash(flinng_index *ix, const float *x, uint64_t ld, uint64_t n,
+             uint32_t *buckets, float *proj, void *ws, size_t ws_bytes);
+// DOPH + bucket combine: buckets n x L; values (optional) n x P.
+int doph_hash(flinng_index *ix, const uint64_t *off, const uint32_t *elems,
+              uint64_t n, uint32_t *buckets, uint32_t *values);
+
+// ---- build.cu
+size_t perm_check_workspace_bytes(uint32_t R, uint64_t n);
+int check_perm(flinng_index *ix, const uint32_t *perm, uint64_t n, void *ws);
+size_t insert_workspace_bytes(const flinng_index *ix);
+int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *perm,
+                  uint64_t n, void *ws);
+
+// ---- query.cu
+int query_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
+                 const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
+                 uint8_t *out_scores);
+int counts_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
+                  uint8_t *out_counts);
+
+}  // namespace flinng

@@ -1,0 +1,272 @@
+"""Python binding of libflinng.so (C ABI in ``include/flinng.h``).
+
+Argument marshalling only: every step of hashing, index construction and
+querying runs in the library's CUDA kernels. The ``flinng_*`` functions here
+carry the C names; ``Index`` wraps them for numpy arrays (host memory) and
+torch CUDA tensors (device memory, on the index's stream).
+
+There is no fallback: if the compiled library is missing or no CUDA device
+is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT = range(6)
+COSINE_SRP, JACCARD_DOPH = 0, 1
+PREC_FP32 = 0
+
+
+class flinng_config(C.Structure):
+    _fields_ = [("metric", C.c_uint32), ("dim", C.c_uint32), ("R", C.c_uint32),
+                ("B", C.c_uint32), ("L", C.c_uint32), ("K", C.c_uint32),
+                ("range_bits", C.c_uint32), ("min_threshold", C.c_uint32),
+                ("precision", C.c_uint32), ("reserved", C.c_uint32),
+                ("capacity", C.c_uint64)]
+
+
+class flinng_params(C.Structure):
+    _fields_ = [("srp_w", C.c_void_p), ("doph_a", C.c_uint32), ("doph_b", C.c_uint32),
+                ("doph_seed", C.c_uint64), ("bucket_a", C.c_void_p), ("bucket_c", C.c_void_p)]
+
+
+class flinng_points(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("ld", C.c_uint64), ("off", C.c_void_p),
+                ("elems", C.c_void_p)]
+
+
+# Every symbol the header declares, with its C signature.
+_SIGS = {
+    "flinng_create": (C.c_int, [C.POINTER(flinng_config), C.POINTER(flinng_params), C.c_void_p,
+                                C.POINTER(C.c_void_p)]),
+    "flinng_build": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint64, C.c_void_p, C.c_int]),
+    "flinng_insert": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint64, C.c_void_p, C.c_int]),
+    "flinng_query": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint32, C.c_void_p,
+                               C.c_uint32, C.c_void_p, C.c_void_p, C.c_int]),
+    "flinng_destroy": (C.c_int, [C.c_void_p]),
+    "flinng_last_error": (C.c_char_p, []),
+    "flinng_size": (C.c_uint64, [C.c_void_p]),
+    "flinng_device_bytes": (C.c_uint64, [C.c_void_p]),
+    "flinng_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "flinng_hash": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint64, C.c_void_p,
+                              C.c_void_p, C.c_void_p, C.c_int]),
+    "flinng_query_buckets": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32,
+                                       C.c_void_p, C.c_void_p, C.c_int]),
+    "flinng_counts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_int]),
+    "flinng_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64,
+                                C.POINTER(C.c_uint64), C.c_void_p]),
+    "flinng_hash_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libflinng.so (built by ``_build.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libflinng.so not found at {path}: build it with "
+                           "paper_2106_11565_gb300._build.build() (nvcc, sm_103a)")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class FlinngError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise FlinngError(rc, load().flinng_last_error().decode())
+
+
+def __getattr__(name):
+    # flinng_* functions resolve to the loaded library's symbols
+    if name.startswith("flinng_") and name in _SIGS:
+        return getattr(load(), name)
+    raise AttributeError(name)
+
+
+# --------------------------------------------------------------------------
+# buffer helpers: numpy -> host pointers, torch CUDA tensors -> device pointers
+# --------------------------------------------------------------------------
+
+def _is_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_cuda(a):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    assert isinstance(a, np.ndarray) and a.flags.c_contiguous
+    return a.ctypes.data
+
+
+def _np(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class Index:
+    """A FLINNG index on the current CUDA device.
+
+    ``metric``: "cosine" (dense fp32 vectors, SRP) or "jaccard" (sets, DOPH).
+    ``params``: from ``workloads.srp_projections`` (cosine: the (L*K, dim)
+    matrix) or ``workloads.doph_params`` (jaccard: dict).
+    """
+
+    def __init__(self, metric: str, R: int, B: int, L: int, K: int, capacity: int,
+                 params, dim: int = 0, W: int | None = None, t_min: int = 1, stream=None):
+        self.lib = load()
+        self.metric = metric
+        self.cfg = flinng_config()
+        self.cfg.metric = COSINE_SRP if metric == "cosine" else JACCARD_DOPH
+        self.cfg.dim = dim
+        self.cfg.R, self.cfg.B, self.cfg.L, self.cfg.K = R, B, L, K
+        self.cfg.range_bits = K if W is None else W
+        self.cfg.min_threshold = t_min
+        self.cfg.precision = PREC_FP32
+        self.cfg.capacity = capacity
+        self.R, self.B, self.L, self.K, self.W = R, B, L, K, self.cfg.range_bits
+        p = flinng_params()
+        keep = []
+        if metric == "cosine":
+            w = _np(params, np.float32)
+            keep.append(w)
+            p.srp_w = w.ctypes.data
+        else:
+            ba = _np(params["bucket_a"], np.uint64)
+            bc = _np(params["bucket_c"], np.uint64)
+            keep += [ba, bc]
+            p.doph_a, p.doph_b, p.doph_seed = params["doph_a"], params["doph_b"], params["doph_seed"]
+            p.bucket_a, p.bucket_c = ba.ctypes.data, bc.ctypes.data
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        h = C.c_void_p()
+        _check(self.lib.flinng_create(C.byref(self.cfg), C.byref(p), C.c_void_p(stream), C.byref(h)))
+        self.h = h
+
+    # ---- lifecycle
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.flinng_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def size(self) -> int:
+        return int(self.lib.flinng_size(self.h))
+
+    @property
+    def device_bytes(self) -> int:
+        return int(self.lib.flinng_device_bytes(self.h))
+
+    # ---- points
+    def _points(self, pts):
+        fp = flinng_points()
+        if pts is None:
+            return fp, 0, 1, []
+        if self.metric == "cosine":
+            x = pts if _is_cuda(pts) else _np(pts, np.float32)
+            fp.x = _ptr(x)
+            fp.ld = x.shape[1]
+            return fp, x.shape[0], int(_is_cuda(x)), [x]
+        off, el = pts
+        if _is_cuda(off):
+            fp.off, fp.elems = _ptr(off), _ptr(el)
+            return fp, off.shape[0] - 1, 1, [off, el]
+        off = _np(off, np.uint64)
+        el = _np(el, np.uint32) if len(el) else np.zeros(1, np.uint32)
+        fp.off, fp.elems = off.ctypes.data, el.ctypes.data
+        return fp, off.shape[0] - 1, 0, [off, el]
+
+    def build(self, pts, perm):
+        fp, n, dev, keep = self._points(pts)
+        perm = perm if _is_cuda(perm) else _np(perm, np.uint32)
+        _check(self.lib.flinng_build(self.h, C.byref(fp), n, _ptr(perm), dev))
+
+    def insert(self, pts, perm):
+        fp, n, dev, keep = self._points(pts)
+        perm = perm if _is_cuda(perm) else _np(perm, np.uint32)
+        _check(self.lib.flinng_insert(self.h, C.byref(fp), n, _ptr(perm), dev))
+
+    def _out(self, dev, shape, dt):
+        if dev:
+            import torch
+            tdt = {np.uint32: torch.int32, np.uint8: torch.uint8, np.float32: torch.float32}[dt]
+            return torch.empty(shape, dtype=tdt, device="cuda")
+        return np.zeros(shape, dt)
+
+    def hash(self, pts, values: bool = False, proj: bool = False):
+        fp, n, dev, keep = self._points(pts)
+        P = self.L * self.K
+        b = self._out(dev, (n, self.L), np.uint32)
+        v = self._out(dev, (n, P), np.uint32) if values and self.metric != "cosine" else None
+        pr = self._out(dev, (n, P), np.float32) if proj and self.metric == "cosine" else None
+        _check(self.lib.flinng_hash(self.h, C.byref(fp), n, _ptr(b), _ptr(v), _ptr(pr), dev))
+        return b, v, pr
+
+    def query(self, q, k_max: int, k=None):
+        fp, nq, dev, keep = self._points(q)
+        ids = self._out(dev, (nq, k_max), np.uint32)
+        sc = self._out(dev, (nq, k_max), np.uint8)
+        kk = None if k is None else (k if _is_cuda(k) else _np(k, np.uint32))
+        _check(self.lib.flinng_query(self.h, C.byref(fp), nq, _ptr(kk), k_max, _ptr(ids), _ptr(sc), dev))
+        return ids, sc
+
+    def query_buckets(self, qb, k_max: int, k=None):
+        dev = int(_is_cuda(qb))
+        qb = qb if dev else _np(qb, np.uint32)
+        nq = qb.shape[0]
+        ids = self._out(dev, (nq, k_max), np.uint32)
+        sc = self._out(dev, (nq, k_max), np.uint8)
+        kk = None if k is None else (k if _is_cuda(k) else _np(k, np.uint32))
+        _check(self.lib.flinng_query_buckets(self.h, _ptr(qb), nq, _ptr(kk), k_max, _ptr(ids),
+                                             _ptr(sc), dev))
+        return ids, sc
+
+    def counts(self, qb):
+        dev = int(_is_cuda(qb))
+        qb = qb if dev else _np(qb, np.uint32)
+        out = self._out(dev, (qb.shape[0], self.B * self.R), np.uint8)
+        _check(self.lib.flinng_counts(self.h, _ptr(qb), qb.shape[0], _ptr(out), dev))
+        return out
+
+    def export(self) -> dict:
+        nc = C.c_uint64()
+        _check(self.lib.flinng_export(self.h, None, None, 0, C.byref(nc), None))
+        off = np.zeros((self.L << self.W) + 1, np.uint32)
+        cells = np.zeros(max(int(nc.value), 1), np.uint16)
+        gid = np.zeros((max(self.size, 1), self.R), np.uint16)
+        _check(self.lib.flinng_export(self.h, off.ctypes.data, cells.ctypes.data, cells.size,
+                                      C.byref(nc), gid.ctypes.data))
+        return {"off": off, "cells": cells[: nc.value], "gid": gid[: self.size]}
+
+    def hash_stats(self):
+        a, b = C.c_uint64(), C.c_uint64()
+        _check(self.lib.flinng_hash_stats(self.h, C.byref(a), C.byref(b)))
+        return int(a.value), int(b.value)

@@ -1,0 +1,252 @@
+"""GPU path vs the CPU oracle, through the C ABI.
+
+Integer results (hash codes, MinHash values, buckets, group ids, the reverse
+index, counts, top-k ids and scores) must be bit-exact. The one
+floating-point quantity, the SRP projection, must be within 1e-5 of the fp64
+oracle relative to ||w|| ||x|| before its sign is taken (the sign itself is
+exact).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2106_11565_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch  # noqa: F401
+    from paper_2106_11565_gb300 import _build, flinng
+    _build.build()
+    return flinng
+
+
+def u32(a):
+    if hasattr(a, "is_cuda"):
+        a = a.cpu().numpy()
+    return np.asarray(a).view(np.uint32) if a.dtype == np.int32 else np.asarray(a)
+
+
+# ------------------------------------------------------------------ cases
+
+def dense_case(seed, N, d, nq, R, B, L, K, n_centers=100):
+    pts, _ = WL.gaussian_mixture(seed, N, d, n_centers, 0.1)
+    q, _ = WL.noisy_queries(seed, pts, nq, 0.05)
+    w = WL.srp_projections(seed, L * K, d)
+    perm = WL.group_permutations(seed, R, N)
+    return pts, q, w, perm
+
+
+def sets_case(seed, N, nq, R, L, K):
+    g = WL.genomic_reads(seed, ref_len=200_000, n_reads=N, read_len=300, n_queries=nq)
+    dp = WL.doph_params(seed, L, K)
+    perm = WL.group_permutations(seed, R, N)
+    return (g["off"], g["elems"]), (g["q_off"], g["q_elems"]), dp, perm
+
+
+def ragged_sets(seed, n):
+    rng = np.random.default_rng(seed)
+    rows = []
+    for i in range(n):
+        s = int(rng.choice([0, 1, 2, 5, 31, 32, 33, 64, 200, 1000]))
+        rows.append(rng.integers(0, 1 << 32, size=s, dtype=np.uint64).astype(np.uint32))
+    return WL.csr_from_rows(rows)
+
+
+# ------------------------------------------------------------------ hashing
+
+@pytest.mark.parametrize("n,d,L,K", [(300, 128, 16, 12), (257, 67, 5, 7), (64, 1, 3, 20), (1, 4096, 2, 16)])
+def test_srp_codes_bit_exact_and_projection_tolerance(F, n, d, L, K):
+    pts, _, w, _ = dense_case(1, n, d, 1, 1, 1, L, K)
+    # plant exact and near cancellations
+    for i in range(0, n, 5):
+        j = i % (L * K)
+        if d > 1:
+            pts[i, -1] = np.float32(-float(np.dot(w[j, :-1].astype(np.float64), pts[i, :-1])) / float(w[j, -1]))
+    pts[n - 1] = 0.0
+    ix = F.Index("cosine", 1, 1, L, K, capacity=n, params=w, dim=d)
+    codes, _, proj = ix.hash(pts, proj=True)
+    ocodes, oproj, _ = O.srp_codes(pts, w, L, K, want_proj=True)
+    assert np.array_equal(u32(codes), ocodes)
+    scale = np.linalg.norm(pts.astype(np.float64), axis=1)[:, None] * \
+        np.linalg.norm(w.astype(np.float64), axis=1)[None, :]
+    rel = np.abs(proj.astype(np.float64) - oproj) / np.maximum(scale, 1e-300)
+    assert rel.max() <= 1e-5
+    nre, nex = ix.hash_stats()
+    assert nre >= n // 5 and nex >= 1       # planted zeros went to the exact path
+
+
+def test_srp_device_and_host_paths_agree(F):
+    import torch
+    pts, _, w, _ = dense_case(2, 500, 96, 1, 1, 1, 8, 10)
+    ix = F.Index("cosine", 1, 1, 8, 10, capacity=500, params=w, dim=96)
+    h, _, _ = ix.hash(pts)
+    dvc, _, _ = ix.hash(torch.from_numpy(pts).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(u32(h), u32(dvc))
+
+
+@pytest.mark.parametrize("L,K,W", [(32, 2, 17), (64, 1, 17), (3, 5, 9), (1, 1, 1)])
+def test_doph_values_and_buckets_bit_exact(F, L, K, W):
+    off, el = ragged_sets(3, 400)
+    dp = WL.doph_params(3, L, K)
+    ix = F.Index("jaccard", 1, 1, L, K, capacity=400, params=dp, W=W)
+    b, v, _ = ix.hash((off, el), values=True)
+    ov = O.doph(off, el, L * K, dp["doph_a"], dp["doph_b"], dp["doph_seed"])
+    ob = O.minhash_buckets(ov, L, K, dp["bucket_a"], dp["bucket_c"], W)
+    assert np.array_equal(u32(v), ov)
+    assert np.array_equal(u32(b), ob)
+
+
+# ------------------------------------------------------------------ index
+
+def oracle_index(metric, R, B, L, K, W, params, pts, perm, t_min=1):
+    idx = O.OracleIndex(metric, R, B, L, K, W, t_min=t_min,
+                        srp_w=params if metric == "cosine" else None,
+                        doph=params if metric != "cosine" else None)
+    idx.build(pts, perm)
+    return idx
+
+
+@pytest.mark.parametrize("R,B", [(3, 100), (1, 1), (4, 7), (2, 1000)])
+def test_build_reverse_index_bit_exact(F, R, B):
+    N, d, L, K = 2000, 32, 6, 8
+    pts, _, w, perm = dense_case(4, N, d, 1, R, B, L, K)
+    ix = F.Index("cosine", R, B, L, K, capacity=N, params=w, dim=d)
+    ix.build(pts, perm)
+    ex = ix.export()
+    o = oracle_index("cosine", R, B, L, K, K, w, pts, perm)
+    assert np.array_equal(ex["gid"], o.gid)
+    assert np.array_equal(ex["off"], o.off)
+    assert np.array_equal(ex["cells"], o.cells)
+
+
+def test_build_rejects_bad_permutation_and_capacity(F):
+    pts, _, w, perm = dense_case(5, 100, 8, 1, 2, 10, 2, 4)
+    ix = F.Index("cosine", 2, 10, 2, 4, capacity=100, params=w, dim=8)
+    bad = perm.copy()
+    bad[1, 3] = bad[1, 4]
+    with pytest.raises(F.FlinngError) as e:
+        ix.build(pts, bad)
+    assert e.value.code == F.ERR_INVALID_ARG
+    bad[1, 3] = 100
+    with pytest.raises(F.FlinngError):
+        ix.build(pts, bad)
+    ix.build(pts, perm)
+    with pytest.raises(F.FlinngError) as e:
+        ix.insert(pts[:1], np.zeros((2, 1), np.uint32))
+    assert e.value.code == F.ERR_CAPACITY
+    assert ix.size == 100
+
+
+def test_insert_equals_oracle_insert(F):
+    N1, N2, d, R, B, L, K = 700, 300, 24, 3, 37, 5, 9
+    pts, q, w, perm = dense_case(6, N1 + N2, d, 50, R, B, L, K)
+    p1 = WL.group_permutations(6, R, N1)
+    p2 = WL.group_permutations(6, R, N2, batch=1)
+    ix = F.Index("cosine", R, B, L, K, capacity=N1 + N2, params=w, dim=d)
+    ix.build(pts[:N1], p1)
+    ix.insert(pts[N1:], p2)
+    o = O.OracleIndex("cosine", R, B, L, K, K, srp_w=w)
+    o.build(pts[:N1], p1)
+    o.insert(pts[N1:], p2)
+    ex = ix.export()
+    assert np.array_equal(ex["gid"], o.gid)
+    assert np.array_equal(ex["off"], o.off) and np.array_equal(ex["cells"], o.cells)
+    ids, sc = ix.query(q, 20)
+    oids, osc = o.query(q, 20)
+    assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)
+
+
+# ------------------------------------------------------------------ query
+
+def test_counts_bit_exact(F):
+    N, d, R, B, L, K = 3000, 64, 3, 100, 16, 12
+    pts, q, w, perm = dense_case(7, N, d, 64, R, B, L, K)
+    ix = F.Index("cosine", R, B, L, K, capacity=N, params=w, dim=d)
+    ix.build(pts, perm)
+    o = oracle_index("cosine", R, B, L, K, K, w, pts, perm)
+    qb = O.srp_codes(q, w, L, K)
+    got = ix.counts(qb)
+    for i in range(q.shape[0]):
+        assert np.array_equal(got[i], O.counts(o.off, o.cells, L, K, qb[i], B * R))
+
+
+@pytest.mark.parametrize("t_min", [1, 3])
+def test_query_dense_bit_exact(F, t_min):
+    N, d, R, B, L, K = 10_000, 128, 3, 100, 16, 12      # the paper-shaped cosine config
+    pts, q, w, perm = dense_case(WL.config_seed(1), N, d, 100, R, B, L, K)
+    ix = F.Index("cosine", R, B, L, K, capacity=N, params=w, dim=d, t_min=t_min)
+    ix.build(pts, perm)
+    o = oracle_index("cosine", R, B, L, K, K, w, pts, perm, t_min=t_min)
+    ids, sc = ix.query(q, 10)
+    oids, osc = o.query(q, 10)
+    assert np.array_equal(u32(ids), oids)
+    assert np.array_equal(sc, osc)
+
+
+def test_query_ragged_k_and_edge_cases(F):
+    N, d, R, B, L, K = 1500, 32, 2, 40, 8, 6
+    pts, q, w, perm = dense_case(8, N, d, 97, R, B, L, K)
+    ix = F.Index("cosine", R, B, L, K, capacity=N, params=w, dim=d)
+    ix.build(pts, perm)
+    o = oracle_index("cosine", R, B, L, K, K, w, pts, perm)
+    rng = np.random.default_rng(8)
+    k = rng.integers(0, 301, size=q.shape[0]).astype(np.uint32)
+    k[:3] = [0, 1, 300]
+    ids, sc = ix.query(q, 300, k=k)
+    oids, osc = o.query(q, 300, k=k)
+    assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)
+    # k larger than the index: every point with score >= t_min, then padding
+    ids, sc = ix.query(q[:5], 1024)
+    oids, osc = o.query(q[:5], 1024)
+    assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)
+    # a query equal to an indexed point returns it with score L
+    ids, sc = ix.query(pts[:20], 5)
+    for i in range(20):
+        assert sc[i, 0] == L
+    with pytest.raises(F.FlinngError):
+        ix.query(q, 10, k=np.full(q.shape[0], 11, np.uint32))
+
+
+def test_query_empty_index_and_empty_batch(F):
+    w = WL.srp_projections(9, 4 * 3, 8)
+    ix = F.Index("cosine", 2, 5, 4, 3, capacity=10, params=w, dim=8)
+    q = np.ones((3, 8), np.float32)
+    ids, sc = ix.query(q, 4)
+    assert np.all(u32(ids) == 0xFFFFFFFF) and np.all(sc == 0)
+    ids, sc = ix.query(np.zeros((0, 8), np.float32), 4)
+    assert ids.shape == (0, 4)
+
+
+def test_query_sets_bit_exact(F):
+    N, nq, R, B, L, K, W = 4000, 200, 2, 1000, 32, 2, 17
+    pts, q, dp, perm = sets_case(10, N, nq, R, L, K)
+    ix = F.Index("jaccard", R, B, L, K, capacity=N, params=dp, W=W)
+    ix.build(pts, perm)
+    o = oracle_index("jaccard", R, B, L, K, W, dp, pts, perm)
+    ex = ix.export()
+    assert np.array_equal(ex["off"], o.off) and np.array_equal(ex["cells"], o.cells)
+    ids, sc = ix.query(q, 100)
+    oids, osc = o.query(q, 100)
+    assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)
+
+
+def test_query_device_buffers_match_host(F):
+    import torch
+    N, nq, R, B, L, K, W = 3000, 100, 2, 300, 16, 2, 12
+    pts, q, dp, perm = sets_case(11, N, nq, R, L, K)
+    ix = F.Index("jaccard", R, B, L, K, capacity=N, params=dp, W=W)
+    ix.build((torch.from_numpy(pts[0].view(np.int64)).cuda(), torch.from_numpy(pts[1].view(np.int32)).cuda()),
+             torch.from_numpy(perm.view(np.int32)).cuda())
+    torch.cuda.synchronize()
+    hid, hsc = ix.query(q, 50)
+    did, dsc = ix.query((torch.from_numpy(q[0].view(np.int64)).cuda(),
+                         torch.from_numpy(q[1].view(np.int32)).cuda()), 50)
+    torch.cuda.synchronize()
+    assert np.array_equal(u32(hid), u32(did)) and np.array_equal(hsc, dsc.cpu().numpy())
+    o = oracle_index("jaccard", R, B, L, K, W, dp, pts, perm)
+    oids, osc = o.query(q, 50)
+    assert np.array_equal(u32(hid), oids)
