@@ -61,6 +61,7 @@ _SIGS = {
     "flinng_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64,
                                 C.POINTER(C.c_uint64), C.c_void_p]),
     "flinng_hash_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    "flinng_kernel_launches": (C.c_uint64, []),
 }
 
 _lib = None
@@ -110,10 +111,15 @@ def _is_cuda(a) -> bool:
     return hasattr(a, "is_cuda") and a.is_cuda
 
 
+def kernel_launches() -> int:
+    """Kernels launched by libflinng.so in this process so far."""
+    return int(load().flinng_kernel_launches())
+
+
 def _ptr(a):
     if a is None:
         return None
-    if _is_cuda(a):
+    if hasattr(a, "data_ptr"):          # torch tensor: CUDA (device) or CPU/pinned (host)
         assert a.is_contiguous()
         return a.data_ptr()
     assert isinstance(a, np.ndarray) and a.flags.c_contiguous
