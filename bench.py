@@ -1,0 +1,578 @@
+#!/usr/bin/env python
+"""FLINNG batched-query benchmark on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload C2] [--impl ours|reference]
+
+One step = one batch of queries through the whole query path: LSH hashing of
+the batch, then the fused count / group-test / AND-over-R decode / top-k
+kernel, inputs resident in HBM, L2 flushed before every step. The index build
+(hash + group assignment + reverse index) is timed the same way and
+reported beside it. Prints one JSON line (rank 0).
+
+Workloads (synthetic, seeded, shaped like the paper's datasets):
+  C1  cosine/SRP, 10,000 Gaussian-mixture vectors d=128, R3 B100 L16 K12,
+      100 queries, k=10
+  C2  Jaccard/MinHash, 100,000 reads of 1,000 bp from a 5 Mbp random ACGT
+      reference with 1-10% substitutions as 18-mer sets, R2 B1000 L32 K2 W17,
+      1,000 held-out reads as queries, k=100        (default)
+
+``--impl reference`` times the CPU oracle on the same workload instead
+(single core, a bounded sample of queries per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2106_11565_gb300 import workloads as WL  # noqa: E402
+
+METRIC = ("queries/s at recall@10≥0.9 on 1 GB300, serving vs plain form; "
+          "p50/p99 latency")
+UNIT = "queries/s"
+
+WORKLOADS = {
+    "C1": dict(metric="cosine", N=10_000, d=128, n_centers=100, sigma=0.1, nq=100,
+               qsigma=0.05, R=3, B=100, L=16, K=12, W=12, k=10,
+               desc="cosine/SRP N=10000 d=128 R3 B100 L16 K12 nq=100 k=10"),
+    "C2": dict(metric="jaccard", ref_len=5_000_000, N=100_000, read_len=1000, kmer=18,
+               nq=1000, R=2, B=1000, L=32, K=2, W=17, k=100,
+               desc="Jaccard/DOPH genomic reads N=100000 len=1000 18-mers R2 B1000 L32 K2 W17 "
+                    "nq=1000 k=100"),
+}
+
+
+# --------------------------------------------------------------------------
+# workload construction and exact ground truth
+# --------------------------------------------------------------------------
+
+def make_workload(name: str) -> dict:
+    c = dict(WORKLOADS[name])
+    seed = WL.config_seed(int(name[1:]))
+    if c["metric"] == "cosine":
+        pts, _ = WL.gaussian_mixture(seed, c["N"], c["d"], c["n_centers"], c["sigma"])
+        q, _ = WL.noisy_queries(seed, pts, c["nq"], c["qsigma"])
+        c.update(pts=pts, q=q, params=WL.srp_projections(seed, c["L"] * c["K"], c["d"]))
+    else:
+        g = WL.genomic_reads(seed, c["ref_len"], c["N"], c["read_len"], c["nq"], kmer=c["kmer"])
+        c.update(pts=(g["off"], g["elems"]), q=(g["q_off"], g["q_elems"]),
+                 params=WL.doph_params(seed, c["L"], c["K"]))
+    c["perm"] = WL.group_permutations(seed, c["R"], c["N"])
+    c["seed"] = seed
+    return c
+
+
+def exact_similarity_topk(c: dict, topn: int = 100):
+    """Exact top-``topn`` neighbours per query: cosine by fp64 brute force;
+    Jaccard through an inverted index over set elements (as the paper
+    computes its genomic and URL ground truth). Returns (ids, sims)."""
+    nq = c["nq"]
+    if c["metric"] == "cosine":
+        x = c["pts"].astype(np.float64)
+        x /= np.maximum(np.linalg.norm(x, axis=1, keepdims=True), 1e-300)
+        q = c["q"].astype(np.float64)
+        q /= np.maximum(np.linalg.norm(q, axis=1, keepdims=True), 1e-300)
+        s = q @ x.T
+        ids = np.argsort(-s, axis=1, kind="stable")[:, :topn]
+        return ids, np.take_along_axis(s, ids, axis=1)
+    off, el = c["pts"]
+    qoff, qel = c["q"]
+    sizes = np.diff(off.astype(np.int64))
+    owner = np.repeat(np.arange(len(sizes)), sizes)
+    order = np.argsort(el, kind="stable")
+    el_s, own_s = el[order], owner[order]
+    ids = np.full((nq, topn), -1, np.int64)
+    sims = np.zeros((nq, topn))
+    for i in range(nq):
+        qe = qel[qoff[i]:qoff[i + 1]]
+        lo = np.searchsorted(el_s, qe, "left")
+        hi = np.searchsorted(el_s, qe, "right")
+        cnt = hi - lo
+        if cnt.sum() == 0:
+            continue
+        idx = np.repeat(lo - np.cumsum(np.r_[0, cnt[:-1]]), cnt) + np.arange(cnt.sum())
+        hits = own_s[idx]
+        u, inter = np.unique(hits, return_counts=True)
+        j = inter / (len(qe) + sizes[u] - inter)
+        top = np.lexsort((u, -j))[:topn]
+        ids[i, :len(top)] = u[top]
+        sims[i, :len(top)] = j[top]
+    return ids, sims
+
+
+def recall_scores(c: dict, got_ids: np.ndarray, exact_ids, exact_sims) -> dict:
+    """recall@10: |returned[:10] with similarity >= the 10th exact| / 10 (ties
+    count as hits, padding as misses); R10@k: same over all k returned; R1@k:
+    the exact nearest neighbour is among the k returned."""
+    nq = got_ids.shape[0]
+    r10, r10k, r1k = [], [], []
+    for i in range(nq):
+        t10 = exact_sims[i, 9]
+        top = set(exact_ids[i, :10].tolist())
+        sim_of = dict(zip(exact_ids[i].tolist(), exact_sims[i].tolist()))
+        ret = [int(x) for x in got_ids[i] if x != 0xFFFFFFFF]
+
+        def hits(lst):
+            return min(10, sum(1 for x in lst if x in top or sim_of.get(x, -1.0) >= t10 > 0))
+        r10.append(hits(ret[:10]) / 10)
+        r10k.append(hits(ret) / 10)
+        r1k.append(1.0 if int(exact_ids[i, 0]) in ret else 0.0)
+    return {"recall_at_10": float(np.mean(r10)), "recall_10_at_k": float(np.mean(r10k)),
+            "recall_1_at_k": float(np.mean(r1k))}
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes (the work the method must do, not a dense scan)
+# --------------------------------------------------------------------------
+
+def query_kernel_bytes(c: dict, ex: dict, counts: np.ndarray, qb: np.ndarray, kq: int) -> dict:
+    """Per-launch algorithmic bytes of the fused query kernel, following its
+    level walk exactly: query buckets L*4, table offsets L*8, bucket lists
+    2 B per cell, then for every repetition-0 cell at count >= the stopping
+    level its member range (8 B) and per member 4 B id + 2(R-1) B group ids,
+    plus k * 5 B of output."""
+    R, B, L, W = c["R"], c["B"], c["L"], c["W"]
+    gid = ex["gid"].astype(np.int64)
+    off = ex["off"]
+    sizes0 = np.bincount(gid[:, 0], minlength=B)
+    total = 0
+    members = 0
+    for i in range(qb.shape[0]):
+        slots = (np.arange(L, dtype=np.int64) << W) | qb[i].astype(np.int64)
+        lists = int((off[slots + 1].astype(np.int64) - off[slots]).sum())
+        cnt = counts[i].astype(np.int64)
+        cell = gid + (np.arange(R) * B)[None, :]
+        score = cnt[cell].min(axis=1)
+        hist = np.bincount(score, minlength=L + 1)
+        ge = np.cumsum(hist[::-1])[::-1]          # points with score >= t
+        tstop = 1
+        for t in range(L, 0, -1):
+            if ge[t] >= kq:
+                tstop = t
+                break
+        c0 = cnt[:B]
+        enum_cells = np.nonzero(c0 >= tstop)[0]
+        m = int(sizes0[enum_cells].sum())
+        members += m
+        total += L * 4 + L * 8 + lists * 2 + len(enum_cells) * 8 + m * (4 + 2 * (R - 1)) + kq * 5
+    return {"bytes": total, "members": members}
+
+
+def hash_kernel_bytes(c: dict) -> int:
+    """Per-launch algorithmic bytes of hashing the query batch."""
+    L = c["L"]
+    if c["metric"] == "cosine":
+        return c["nq"] * c["d"] * 4 + c["L"] * c["K"] * c["d"] * 4 + c["nq"] * L * 4
+    qoff, qel = c["q"]
+    return int(qel.size) * 4 + (c["nq"] + 1) * 8 + c["nq"] * L * 4
+
+
+# --------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi every 50 ms.
+
+    The sampler starts before a busy warm-up phase that runs the same kernels
+    back to back right up to the timed region, so that short timed regions
+    still have samples taken under this load; ``stop`` keeps the samples
+    from the loaded window [load_start, timed_end + 0.1 s]."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    @staticmethod
+    def _ts(s: str) -> float:
+        import datetime
+        s = s.strip()
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(s, fmt).timestamp()
+            except ValueError:
+                pass
+        return float("nan")
+
+    def stop(self, t_from: float, t_to: float) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        win = [r for r in rows if t_from - 0.05 <= self._ts(r[0]) <= t_to + 0.1]
+        if not win:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[1]) for r in win) if v is not None]
+        mx = [v for v in (num(r[2]) for r in win) if v is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in win for j in range(4) if r[5 + j].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(win),
+                "window": "busy warm-up under the same kernels + timed region"}
+
+
+# --------------------------------------------------------------------------
+# traffic recorded by ncu (profiles/), valid only for the unchanged kernel
+# --------------------------------------------------------------------------
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("query.cu", "internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2106_11565_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    path = os.path.join(ROOT, "profiles", f"k_query_{workload}_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing
+# --------------------------------------------------------------------------
+
+def oracle_index(c: dict):
+    from oracle import oracle as O
+    o = O.OracleIndex(c["metric"], c["R"], c["B"], c["L"], c["K"], c["W"],
+                      srp_w=c["params"] if c["metric"] == "cosine" else None,
+                      doph=c["params"] if c["metric"] != "cosine" else None)
+    o.build(c["pts"], c["perm"])
+    return o
+
+
+def query_slice(c: dict, lo: int, hi: int):
+    if c["metric"] == "cosine":
+        return c["q"][lo:hi]
+    qoff, qel = c["q"]
+    off = qoff[lo:hi + 1] - qoff[lo]
+    return off, qel[qoff[lo]:qoff[hi]]
+
+
+def time_oracle_queries(o, c: dict, target_s: float = 10.0, max_rounds: int = 10_000):
+    """Oracle queries/s on one core over whole passes of the query batch,
+    repeated until about ``target_s`` seconds of CPU work."""
+    t0 = time.perf_counter()
+    n = 0
+    rounds = 0
+    while True:
+        o.query(c["q"], c["k"])
+        n += c["nq"]
+        rounds += 1
+        el = time.perf_counter() - t0
+        if el >= target_s or rounds >= max_rounds:
+            break
+    return n / el, n, el
+
+
+# --------------------------------------------------------------------------
+# main arm
+# --------------------------------------------------------------------------
+
+def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
+    import torch
+    from paper_2106_11565_gb300 import _build
+    from paper_2106_11565_gb300 import flinng as F
+    _build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    nq, k, L = c["nq"], c["k"], c["L"]
+
+    ix = F.Index(c["metric"], c["R"], c["B"], L, c["K"], capacity=c["N"], params=c["params"],
+                 dim=c.get("d", 0), W=c["W"])
+
+    def to_dev_points(p):
+        if c["metric"] == "cosine":
+            return torch.from_numpy(p).to(dev)
+        off, el = p
+        return (torch.from_numpy(off.view(np.int64)).to(dev), torch.from_numpy(el.view(np.int32)).to(dev))
+
+    d_pts = to_dev_points(c["pts"])
+    d_q = to_dev_points(c["q"])
+    d_perm = torch.from_numpy(c["perm"].view(np.int32)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)   # > L2 (129 MB)
+
+    # ---- build: warm-up then timed (each build replaces the index)
+    build_ms = []
+    for it in range(2 + 3):
+        flush.fill_(it)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix.build(d_pts, d_perm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 2:
+            build_ms.append(e0.elapsed_time(e1))
+
+    # ---- staged buffers for the query step
+    qb = torch.empty((nq, L), dtype=torch.int32, device=dev)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    sc = torch.empty((nq, k), dtype=torch.uint8, device=dev)
+    fp, n_, devflag, keep = ix._points(d_q)
+    import ctypes as C
+    lib = ix.lib
+
+    def step():
+        F._check(lib.flinng_hash(ix.h, C.byref(fp), nq, qb.data_ptr(), None, None, 1))
+        e_mid.record(stream)
+        F._check(lib.flinng_query_buckets(ix.h, qb.data_ptr(), nq, None, k, ids.data_ptr(),
+                                          sc.data_ptr(), 1))
+
+    # consistency: the staged step equals the single flinng_query call
+    e_mid = torch.cuda.Event(enable_timing=True)
+    step()
+    ids_q, sc_q = ix.query(d_q, k)
+    torch.cuda.synchronize()
+    assert torch.equal(ids, ids_q) and torch.equal(sc, sc_q), "staged step != flinng_query"
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(dev.index)
+    time.sleep(0.3)                                  # nvidia-smi start-up
+    # warm-up: at least W steps, and at least 0.5 s of back-to-back steps so
+    # that the clock samples see this load
+    t_load = time.time()
+    it = 0
+    while it < args.warmup or time.time() - t_load < 0.5:
+        flush.fill_(it)
+        step()
+        if it % 50 == 0:
+            torch.cuda.synchronize()
+        it += 1
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = F.kernel_launches()
+    for it in range(args.steps):
+        flush.fill_(it + 1)                         # evict L2 between steps (not timed)
+        e0, e_mid, e1 = ev[it]
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    launches = F.kernel_launches() - launches0
+    t_end = time.time()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop(t_load, t_end)
+    step_ms = [a.elapsed_time(b) for a, _, b in ev]
+    hash_ms = [a.elapsed_time(m) for a, m, _ in ev]
+    query_ms = [m.elapsed_time(b) for _, m, b in ev]
+    total_ms = float(sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * nq * args.steps / (total_ms / 1e3)
+
+    # ---- e2e: flinng_query with host (pinned) buffers, copies inside the call
+    if c["metric"] == "cosine":
+        h_q = torch.from_numpy(c["q"]).pin_memory().numpy()
+        h2d = h_q.nbytes
+    else:
+        off_p = torch.from_numpy(c["q"][0].view(np.int64)).pin_memory().numpy().view(np.uint64)
+        el_p = torch.from_numpy(c["q"][1].view(np.int32)).pin_memory().numpy().view(np.uint32)
+        h_q = (off_p, el_p)
+        h2d = off_p.nbytes + el_p.nbytes
+    for _ in range(2):
+        ix.query(h_q, k)
+    e2e_s = []
+    for it in range(args.steps):
+        flush.fill_(it)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h_ids, h_sc = ix.query(h_q, k)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_total = float(sum(e2e_s))
+    if dist is not None:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * nq * args.steps / e2e_total
+    d2h = nq * k * 5
+
+    if rank != 0:
+        return None
+
+    # ---- quality, work accounting, roofline
+    out_ids = ids.cpu().numpy().view(np.uint32)
+    if args.no_recall:
+        rec = {"recall_at_10": float("nan"), "note": "not computed (--no-recall)"}
+    else:
+        ex_ids, ex_sims = exact_similarity_topk(c)
+        rec = recall_scores(c, out_ids, ex_ids, ex_sims)
+    ex = ix.export()
+    qb_h = qb.cpu().numpy().view(np.uint32)
+    counts = ix.counts(qb_h)
+    qbytes = query_kernel_bytes(c, ex, counts, qb_h, k)
+    hbytes = hash_kernel_bytes(c)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    q_mean = statistics.mean(query_ms)
+    h_mean = statistics.mean(hash_ms)
+    dom = "k_query" if q_mean >= h_mean else ("k_doph" if c["metric"] != "cosine" else "k_srp_fp32")
+    dom_bytes = qbytes["bytes"] if dom == "k_query" else hbytes
+    dom_ms = q_mean if dom == "k_query" else h_mean
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    traffic = recorded_traffic(args.workload) if dom == "k_query" else None
+    sorted_ms = sorted(step_ms)
+
+    def pct(p):
+        return sorted_ms[min(len(sorted_ms) - 1, int(round(p / 100 * (len(sorted_ms) - 1))))]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32" if c["metric"] != "cosine" else "f32",
+        "data": "synthetic (seeded; stands in for the paper's datasets)",
+        "config": {"workload": f"{args.workload}: {c['desc']}", "form": "plain batched",
+                   "global_batch": world * nq, "k": k, "l2": "flushed before every step (256 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "recall": rec,
+        "recall_target_met": rec["recall_at_10"] >= 0.9,
+        "latency_ms": {"batch_p50": pct(50), "batch_p99": pct(99),
+                       "note": "plain batched form: every query of a batch completes with the batch"},
+        "stages_ms": {"hash": h_mean, "query": q_mean},
+        "build": {"ms": statistics.mean(build_ms), "points_per_s": c["N"] / (statistics.mean(build_ms) / 1e3),
+                  "n_cells": int(ex["off"][-1])},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": dom_bytes,
+                     "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
+                     "members_enumerated_per_query": qbytes["members"] / nq},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "api": "flinng_query, host pinned buffers"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        o = oracle_index(c)
+        qps, n, el = time_oracle_queries(o, c)
+        oids, _ = o.query(c["q"], k)
+        line["parity_vs_oracle"] = bool(np.array_equal(oids, out_ids))
+        line["cpu_baseline"] = {"value": qps, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{n} queries ({n // nq} passes of the batch), {el:.1f} s, "
+                                          "index built beforehand (not timed)"}
+    return line
+
+
+def run_reference(args, c: dict) -> dict:
+    """The CPU oracle as the reference arm: each step is a bounded sample of
+    the query batch on one core."""
+    o = oracle_index(c)
+    per_step = max(1, min(c["nq"], 200))
+    for it in range(args.warmup):
+        o.query(query_slice(c, 0, per_step), c["k"])
+    t = []
+    for it in range(args.steps):
+        lo = (it * per_step) % c["nq"]
+        hi = min(c["nq"], lo + per_step)
+        t0 = time.perf_counter()
+        o.query(query_slice(c, lo, hi), c["k"])
+        t.append((time.perf_counter() - t0, hi - lo))
+    el = sum(a for a, _ in t)
+    n = sum(b for _, b in t)
+    value = n / el
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32" if c["metric"] != "cosine" else "f64",
+        "data": "synthetic (seeded; stands in for the paper's datasets)",
+        "config": {"workload": f"{args.workload}: {c['desc']}", "form": "plain batched",
+                   "global_batch": c["nq"], "k": c["k"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} queries per step, single thread, index built "
+                                   "beforehand (not timed)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-recall", action="store_true", help="skip the exact ground truth (profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        c = make_workload(args.workload)
+        print(json.dumps(run_reference(args, c)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    c = make_workload(args.workload)
+    line = run_ours(args, c, rank, world)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
