@@ -214,6 +214,40 @@ int flinng_hash_stats(const flinng_index *idx, uint64_t *n_recheck,
  * indices, all threads); memset/memcpy operations are not counted. */
 uint64_t flinng_kernel_launches(void);
 
+/*
+ * flinng_query without any device allocation. The paper has no counterpart:
+ * this is a deployment variant of the batched query.
+ *
+ * Who needs it: flinng_query keeps its intermediate query buckets (and, for
+ * cosine indices, its sign re-check list) in a workspace that it grows with
+ * cudaMalloc - after synchronising the stream and freeing the old one -
+ * whenever a batch is larger than any before. Some callers cannot allow
+ * that: a server whose HBM is handed out up front to resident indices and
+ * request slots under a fixed budget, where an allocation at query time can
+ * fail or breach the budget; a latency-critical loop that cannot absorb the
+ * device-wide synchronisation of cudaFree; a host application whose device
+ * memory must come from its own pool. This entry point allocates nothing:
+ * its scratch is one fixed array inside the library (6 MiB per GPU that
+ * loads the library, held until the process exits), the caller passes the
+ * inputs and outputs.
+ *
+ * Arguments and results are those of flinng_query with on_device = 1: q, k,
+ * out_ids and out_scores are device memory; the call is asynchronous on the
+ * index's stream. The index's device must be the current device.
+ * Limits: nq * L <= 262144, and for cosine indices nq * L * K <= 655296.
+ * Larger batches are rejected with FLINNG_ERR_INVALID_ARG (split them, or use
+ * flinng_query).
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents (each
+ * call overwrites what it reads): calls whose GPU work overlaps - on
+ * different streams, or different indices - race on it and must be
+ * serialised by the caller.
+ */
+int flinng_query_noalloc(flinng_index *idx, const flinng_points *q, uint32_t nq,
+                         const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
+                         uint8_t *out_scores);
+
 #ifdef __cplusplus
 }
 #endif

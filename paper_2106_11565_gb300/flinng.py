@@ -62,6 +62,8 @@ _SIGS = {
                                 C.POINTER(C.c_uint64), C.c_void_p]),
     "flinng_hash_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "flinng_kernel_launches": (C.c_uint64, []),
+    "flinng_query_noalloc": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint32, C.c_void_p,
+                                       C.c_uint32, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
