@@ -1,5 +1,5 @@
 // Batched query: collision counts, group tests, AND-over-R decode and top-k
-// (Sec. 5, Alg. 2 and Alg. 3). One CTA per query.
+// (Sec. 5, Alg. 2 and Alg. 3). One CTA of 256 threads per query.
 //
 // Alg. 3 walks cells by count (descending, ties by cell id) and emits a point
 // when the last of its R cells is reached. That order is the ascending order
@@ -9,25 +9,30 @@
 // computes the k smallest keys without the per-point counter array:
 //
 //  1. counts: cnt[c] += 1 for every cell c in the query's list of each table
-//     (bytes in shared memory, L <= 255).
+//     (bytes in shared memory, L <= 255). The L lists are flattened over the
+//     whole CTA.
 //  2. group tests at decreasing thresholds: the cells of repetition 0 are
 //     bucketed by count; level t holds those with count exactly t.
 //  3. decode: walk levels t = L, L-1, ..., t_min. A point of score >= t has
 //     all R cells at count >= t, in particular its repetition-0 cell, so after
-//     level t every point with score >= t has been seen. Each member of a
-//     level-t cell gets its key from its R group ids (the AND over R);
-//     stop once >= k points of score >= t were seen - no unseen point can
-//     precede them.
-//  4. top-k: each warp keeps its own buffer of candidate keys below its
-//     running cutoff, sorted and cut to k when full; the warp buffers are
-//     merged by one block-wide bitonic sort.
+//     level t every point with score >= t has been seen. The members of a
+//     level's cells are flattened over the CTA (coalesced member reads, no
+//     per-cell imbalance); each member's key comes from its R group ids (the
+//     AND over R). Stop once >= k points of score >= t were seen: no unseen
+//     point can precede them.
+//  4. top-k: candidates go to one shared buffer; when it would overflow, a
+//     radix select over the 56-bit keys keeps the k best and tightens the
+//     admission cutoff. At the end a radix select cuts the buffer to k keys,
+//     which a small bitonic sort orders.
 #include "internal.cuh"
 
 namespace flinng {
 
 namespace {
 
-constexpr int kQW = 8;   // warps per query CTA
+constexpr int kQT = 256;                 // threads per query CTA
+constexpr int kQW = kQT / 32;
+constexpr uint64_t kKeyBits = (1ull << 56) - 1;
 
 struct QArgs {
     const uint32_t *qb;
@@ -39,43 +44,60 @@ struct QArgs {
     const uint16_t *gid;
     const uint32_t *moff;
     const uint32_t *mem;
-    uint32_t L, W, R, B, BR, t_min, cw;
+    uint32_t L, W, R, B, BR, t_min;
+    uint32_t cap;      // candidate buffer entries (power of two)
+    uint32_t kp;       // final sort width: power of two >= k_max
     uint32_t *out_ids;
     uint8_t *out_scores;
     uint8_t *out_counts;
 };
 
 struct QSmem {
-    uint64_t *buf;     // kQW * cw keys
-    uint64_t *wcut;    // kQW
-    uint32_t *wn;      // kQW
-    uint32_t *hist_s;  // 256: points seen, by score
-    uint32_t *lvl_n;   // 256: repetition-0 cells per count
-    uint32_t *lvl_cur; // 256
-    uint32_t *cntw;    // (BR + 3) / 4 words of byte counts
-    uint16_t *lvl_cells;   // B
+    uint64_t *buf;       // cap candidate keys
+    uint64_t *keep;      // kp keys (selection output, final sort)
+    uint32_t *u;         // 8 scalars: nbuf, nkeep, sel digit, sel rem, ...
+    uint32_t *hist_s;    // 256: points seen, by score
+    uint32_t *lvl_n;     // 256: repetition-0 cells per count
+    uint32_t *lvl_cur;   // 256
+    uint32_t *rhist;     // 256: radix histogram
+    uint32_t *c_start;   // kQT: member start of each cell of a chunk / list start
+    uint32_t *c_pre;     // kQT + 1: exclusive prefix of member counts
+    uint32_t *wsum;      // kQW: block-scan scratch
+    uint32_t *cntw;      // (BR + 3) / 4 words of byte counts
+    uint16_t *lvl_cells; // B
 };
 
-__host__ __device__ inline size_t qsmem_bytes(uint32_t cw, uint32_t BR, uint32_t B)
+__host__ __device__ inline size_t qsmem_bytes(uint32_t cap, uint32_t kp, uint32_t BR, uint32_t B)
 {
-    size_t b = size_t(kQW) * cw * 8 + kQW * 8 + kQW * 4 + 3 * 256 * 4;
+    size_t b = size_t(cap) * 8 + size_t(kp) * 8 + 8 * 4 + 4 * 256 * 4 + kQT * 4 + (kQT + 1) * 4 + kQW * 4;
+    b = (b + 15) & ~size_t(15);
     b += size_t((BR + 3) / 4) * 4;
     b += size_t(B) * 2;
     return (b + 15) & ~size_t(15);
 }
 
-__device__ inline QSmem carve_q(unsigned char *sm, uint32_t cw, uint32_t BR)
+__device__ inline QSmem carve_q(unsigned char *sm, uint32_t cap, uint32_t kp)
 {
     QSmem s;
     s.buf = (uint64_t *)sm;
-    s.wcut = s.buf + size_t(kQW) * cw;
-    s.wn = (uint32_t *)(s.wcut + kQW);
-    s.hist_s = s.wn + kQW;
+    s.keep = s.buf + cap;
+    s.u = (uint32_t *)(s.keep + kp);
+    s.hist_s = s.u + 8;
     s.lvl_n = s.hist_s + 256;
     s.lvl_cur = s.lvl_n + 256;
-    s.cntw = s.lvl_cur + 256;
-    s.lvl_cells = (uint16_t *)(s.cntw + (BR + 3) / 4);
+    s.rhist = s.lvl_cur + 256;
+    s.c_start = s.rhist + 256;
+    s.c_pre = s.c_start + kQT;
+    s.wsum = s.c_pre + kQT + 1;
+    size_t o = (size_t)((unsigned char *)(s.wsum + kQW) - sm);
+    o = (o + 15) & ~size_t(15);
+    s.cntw = (uint32_t *)(sm + o);
     return s;
+}
+
+__device__ inline uint16_t *lvl_cells_ptr(const QSmem &s, uint32_t BR)
+{
+    return (uint16_t *)(s.cntw + (BR + 3) / 4);
 }
 
 template <int RP>
@@ -97,96 +119,177 @@ __device__ inline void load_gid(const uint16_t *__restrict__ gid, uint32_t x, ui
     }
 }
 
-// Sort wb[0..cw) ascending with one warp after padding entries >= n.
-__device__ void warp_sort(uint64_t *wb, uint32_t n, uint32_t cw, int lane)
+// Exclusive block scan of one value per thread; returns the prefix and
+// writes the total to *total (all threads). Contains __syncthreads.
+__device__ uint32_t block_excl_scan(uint32_t v, uint32_t *wsum, uint32_t *total)
 {
-    for (uint32_t i = lane; i < cw; i += 32)
-        if (i >= n) wb[i] = kKeyNone;
-    __syncwarp();
-    for (uint32_t k = 2; k <= cw; k <<= 1) {
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = lane; i < cw; i += 32) {
-                const uint32_t l = i ^ j;
-                if (l > i) {
-                    const uint64_t a = wb[i], b = wb[l];
-                    const bool up = (i & k) == 0;
-                    if ((a > b) == up) {
-                        wb[i] = b;
-                        wb[l] = a;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kQW; ++w) {
+        const uint32_t t = wsum[w];
+        before += (w < warp) ? t : 0u;
+        all += t;
+    }
+    __syncthreads();
+    *total = all;
+    return before + x - v;
+}
+
+// Largest i in [0, n) with pre[i] <= j (pre ascending, pre[0] = 0 <= j).
+__device__ inline uint32_t find_seg(const uint32_t *pre, uint32_t n, uint32_t j)
+{
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pre[mid] <= j) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Radix select over keys[0..n): returns (prefix, mask) such that exactly kk
+// keys satisfy (key & mask) <= prefix (keys are unique, kk <= n).
+__device__ void block_select(const uint64_t *keys, uint32_t n, uint32_t kk, const QSmem &s,
+                             uint64_t &prefix_out, uint64_t &mask_out)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    uint64_t prefix = 0, mask = 0;
+    uint32_t rem = kk;
+    for (int shift = 48; shift >= 0; shift -= 8) {
+        s.rhist[tid] = 0u;                      // kQT == 256 bins
+        __syncthreads();
+        for (uint32_t i = tid; i < n; i += kQT) {
+            const uint64_t v = keys[i];
+            if ((v & mask) == prefix) atomicAdd(&s.rhist[(v >> shift) & 0xFF], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {
+            uint32_t h[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                h[j] = s.rhist[lane * 8 + j];
+                sum += h[j];
+            }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            uint32_t run = incl - sum;
+            if (run < rem && rem <= incl) {       // exactly one lane holds the digit
+                uint32_t d = 0, hd = 0;
+                bool found = false;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (!found) {
+                        if (run + h[j] >= rem) {
+                            d = lane * 8 + j;
+                            hd = h[j];
+                            found = true;
+                        } else {
+                            run += h[j];
+                        }
                     }
                 }
+                s.u[2] = d;
+                s.u[3] = rem - run;               // rank inside the digit's bucket
+                s.u[4] = (hd == rem - run) ? 1u : 0u;   // the bucket is taken whole
             }
-            __syncwarp();
         }
+        __syncthreads();
+        const uint32_t d = s.u[2];
+        rem = s.u[3];
+        const bool whole = s.u[4] != 0;
+        __syncthreads();
+        prefix |= uint64_t(d) << shift;
+        mask |= uint64_t(0xFF) << shift;
+        if (whole) break;
     }
+    prefix_out = prefix;
+    mask_out = mask;
 }
 
-// Warp-cooperative insertion of one key per lane into the warp's buffer.
-__device__ void warp_insert(uint64_t key, bool has, uint64_t *wb, uint32_t *wn,
-                            uint64_t *wcut, uint32_t kq, uint32_t cw, int lane)
+// Keep the kk best of buf[0..nbuf) in buf[0..kk); returns the new admission
+// bound (keys above it can never enter the top kk).
+__device__ uint64_t block_compact(const QSmem &s, uint32_t nbuf, uint32_t kk)
 {
-    uint64_t cut = *wcut;
-    bool want = has && key < cut;
-    uint32_t m = __ballot_sync(0xffffffffu, want);
-    if (m == 0) return;
-    uint32_t n = *wn;
-    if (n + __popc(m) > cw) {
-        warp_sort(wb, n, cw, lane);
-        if (n > kq) n = kq;
-        if (n == kq) cut = wb[kq - 1];
-        want = has && key < cut;
-        m = __ballot_sync(0xffffffffu, want);
+    uint64_t prefix, mask;
+    block_select(s.buf, nbuf, kk, s, prefix, mask);
+    if (threadIdx.x == 0) s.u[1] = 0u;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nbuf; i += kQT) {
+        const uint64_t v = s.buf[i];
+        if ((v & mask) <= prefix) s.keep[atomicAdd(&s.u[1], 1u)] = v;
     }
-    if (want) wb[n + __popc(m & ((1u << lane) - 1u))] = key;
-    __syncwarp();
-    if (lane == 0) {
-        *wn = n + __popc(m);
-        *wcut = cut;
-    }
-    __syncwarp();
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kk; i += kQT) s.buf[i] = s.keep[i];
+    if (threadIdx.x == 0) s.u[0] = kk;
+    __syncthreads();
+    return prefix | (~mask & kKeyBits);
 }
 
-__device__ void gather_counts(const QArgs &a, const QSmem &s, uint32_t q, int lane, int warp)
+__device__ void gather_counts(const QArgs &a, const QSmem &s, uint32_t q)
 {
-    const uint32_t *qb = a.qb + size_t(q) * a.L;
-    for (uint32_t l = warp; l < a.L; l += kQW) {
-        const uint64_t slot = (uint64_t(l) << a.W) | qb[l];
-        const uint32_t beg = a.off[slot], end = a.off[slot + 1];
-        for (uint32_t t = beg + lane; t < end; t += 32) {
-            const uint32_t c = a.cells[t];
+    const int tid = threadIdx.x;
+    // one thread per table: its list's start and length
+    uint32_t len = 0;
+    for (uint32_t l0 = 0; l0 < a.L; l0 += kQT) {
+        const uint32_t l = l0 + tid;
+        uint32_t beg = 0;
+        len = 0;
+        if (l < a.L) {
+            const uint64_t slot = (uint64_t(l) << a.W) | a.qb[size_t(q) * a.L + l];
+            beg = a.off[slot];
+            len = a.off[slot + 1] - beg;
+        }
+        uint32_t total;
+        const uint32_t pre = block_excl_scan(len, s.wsum, &total);
+        s.c_start[tid] = beg;
+        s.c_pre[tid] = pre;
+        __syncthreads();
+        const uint32_t nl = min(uint32_t(kQT), a.L - l0);
+        for (uint32_t e = tid; e < total; e += kQT) {
+            const uint32_t t = find_seg(s.c_pre, nl, e);
+            const uint32_t c = a.cells[s.c_start[t] + (e - s.c_pre[t])];
             atomicAdd(&s.cntw[c >> 2], 1u << ((c & 3) * 8));
         }
+        __syncthreads();
     }
 }
 
 template <int RP>
-__global__ void __launch_bounds__(kQW * 32)
+__global__ void __launch_bounds__(kQT)
 k_query(QArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
-    const QSmem s = carve_q(sm, a.cw, a.BR);
+    const QSmem s = carve_q(sm, a.cap, a.kp);
+    uint16_t *lvl_cells = lvl_cells_ptr(s, a.BR);
     const uint8_t *cnt8 = reinterpret_cast<const uint8_t *>(s.cntw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nthr = kQW * 32;
+    const int tid = threadIdx.x;
     const uint32_t nwords = (a.BR + 3) / 4;
 
     for (uint32_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
         uint32_t kq = a.k ? a.k[q] : a.k_max;
         if (kq > a.k_max) kq = a.k_max;
-        for (uint32_t i = tid; i < nwords; i += nthr) s.cntw[i] = 0u;
-        for (uint32_t i = tid; i < 256; i += nthr) {
-            s.hist_s[i] = 0u;
-            s.lvl_n[i] = 0u;
-        }
-        if (lane == 0) {
-            s.wn[warp] = 0u;
-            s.wcut[warp] = kKeyNone;
-        }
+        for (uint32_t i = tid; i < nwords; i += kQT) s.cntw[i] = 0u;
+        s.hist_s[tid] = 0u;
+        s.lvl_n[tid] = 0u;
+        if (tid < 8) s.u[tid] = 0u;
         __syncthreads();
         if (kq > 0) {
-            gather_counts(a, s, q, lane, warp);
-            __syncthreads();
-            for (uint32_t b = tid; b < a.B; b += nthr) {
+            gather_counts(a, s, q);
+            // group tests of repetition 0, bucketed by count level
+            for (uint32_t b = tid; b < a.B; b += kQT) {
                 const uint32_t v = cnt8[b];
                 if (v >= a.t_min) atomicAdd(&s.lvl_n[v], 1u);
             }
@@ -194,29 +297,43 @@ k_query(QArgs a)
             if (tid == 0) {
                 uint32_t run = 0;
                 for (int t = int(a.L); t >= int(a.t_min); --t) {
+                    s.lvl_cur[t] = run;
                     run += s.lvl_n[t];
-                    s.lvl_cur[t] = run - s.lvl_n[t];
                 }
             }
             __syncthreads();
-            for (uint32_t b = tid; b < a.B; b += nthr) {
+            for (uint32_t b = tid; b < a.B; b += kQT) {
                 const uint32_t v = cnt8[b];
-                if (v >= a.t_min) s.lvl_cells[atomicAdd(&s.lvl_cur[v], 1u)] = uint16_t(b);
+                if (v >= a.t_min) lvl_cells[atomicAdd(&s.lvl_cur[v], 1u)] = uint16_t(b);
             }
             __syncthreads();
-            uint64_t *wb = s.buf + size_t(warp) * a.cw;
+            // decode, level by level
+            uint64_t bound = kKeyBits;           // admission: key <= bound
+            uint32_t seen = 0;                   // points with score >= current level
+            const uint32_t sub = a.cap - a.kp;   // members per round (room after a compaction)
             for (int t = int(a.L); t >= int(a.t_min); --t) {
                 const uint32_t nc = s.lvl_n[t];
-                const uint32_t start = s.lvl_cur[t] - nc;
-                for (uint32_t ci = warp; ci < nc; ci += kQW) {
-                    const uint32_t b = s.lvl_cells[start + ci];
-                    const uint32_t mb = a.moff[b], me = a.moff[b + 1];
-                    for (uint32_t m0 = mb; m0 < me; m0 += 32) {
-                        const uint32_t m = m0 + lane;
-                        bool has = false;
-                        uint64_t key = kKeyNone;
-                        if (m < me) {
-                            const uint32_t x = __ldg(a.mem + m);
+                const uint32_t first = s.lvl_cur[t] - nc;
+                for (uint32_t c0 = 0; c0 < nc; c0 += kQT) {
+                    const uint32_t ci = c0 + tid;
+                    uint32_t ms = 0, sz = 0;
+                    if (ci < nc) {
+                        const uint32_t b = lvl_cells[first + ci];
+                        ms = a.moff[b];
+                        sz = a.moff[b + 1] - ms;
+                    }
+                    uint32_t M;
+                    const uint32_t pre = block_excl_scan(sz, s.wsum, &M);
+                    s.c_start[tid] = ms;
+                    s.c_pre[tid] = pre;
+                    const uint32_t ncc = min(uint32_t(kQT), nc - c0);
+                    __syncthreads();
+                    for (uint32_t j0 = 0; j0 < M; j0 += sub) {
+                        const uint32_t jn = min(M, j0 + sub);
+                        if (s.u[0] + (jn - j0) > a.cap) bound = block_compact(s, s.u[0], kq);
+                        for (uint32_t j = j0 + tid; j < jn; j += kQT) {
+                            const uint32_t cs = find_seg(s.c_pre, ncc, j);
+                            const uint32_t x = __ldg(a.mem + s.c_start[cs] + (j - s.c_pre[cs]));
                             uint32_t g[RP];
                             load_gid<RP>(a.gid, x, g);
                             uint32_t score = 256, last = 0;
@@ -234,43 +351,45 @@ k_query(QArgs a)
                                 }
                             }
                             if (score >= a.t_min) {
-                                has = true;
-                                key = (uint64_t(255u - score) << 48) | (uint64_t(last) << 32) | x;
                                 atomicAdd(&s.hist_s[score], 1u);
+                                const uint64_t key = (uint64_t(255u - score) << 48) | (uint64_t(last) << 32) | x;
+                                if (key <= bound) s.buf[atomicAdd(&s.u[0], 1u)] = key;
                             }
                         }
-                        warp_insert(key, has, wb, &s.wn[warp], &s.wcut[warp], kq, a.cw, lane);
+                        __syncthreads();
                     }
                 }
-                __syncthreads();
-                uint32_t total = 0;
-                for (uint32_t sc = uint32_t(t); sc <= a.L; ++sc) total += s.hist_s[sc];
-                if (total >= kq) break;
+                seen += s.hist_s[t];             // final: later levels only add scores < t
+                if (seen >= kq) break;
             }
         }
         __syncthreads();
-        const uint32_t T = kQW * a.cw;
-        for (uint32_t i = tid; i < T; i += nthr)
-            if ((i % a.cw) >= s.wn[i / a.cw]) s.buf[i] = kKeyNone;
+        // final top-k: cut to kq keys, sort, write
+        const uint32_t nbuf = s.u[0];
+        const uint32_t nk = nbuf < kq ? nbuf : kq;
+        if (nbuf > kq) {
+            block_compact(s, nbuf, kq);
+        }
+        for (uint32_t i = tid; i < a.kp; i += kQT) s.keep[i] = (i < nk) ? s.buf[i] : kKeyNone;
         __syncthreads();
-        for (uint32_t k = 2; k <= T; k <<= 1) {
-            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = tid; i < T; i += nthr) {
+        for (uint32_t k2 = 2; k2 <= a.kp; k2 <<= 1) {
+            for (uint32_t j = k2 >> 1; j > 0; j >>= 1) {
+                for (uint32_t i = tid; i < a.kp; i += kQT) {
                     const uint32_t l = i ^ j;
                     if (l > i) {
-                        const uint64_t x = s.buf[i], y = s.buf[l];
-                        const bool up = (i & k) == 0;
+                        const uint64_t x = s.keep[i], y = s.keep[l];
+                        const bool up = (i & k2) == 0;
                         if ((x > y) == up) {
-                            s.buf[i] = y;
-                            s.buf[l] = x;
+                            s.keep[i] = y;
+                            s.keep[l] = x;
                         }
                     }
                 }
                 __syncthreads();
             }
         }
-        for (uint32_t i = tid; i < a.k_max; i += nthr) {
-            const uint64_t key = (i < kq) ? s.buf[i] : kKeyNone;
+        for (uint32_t i = tid; i < a.k_max; i += kQT) {
+            const uint64_t key = (i < nk) ? s.keep[i] : kKeyNone;
             const bool ok = key != kKeyNone;
             a.out_ids[size_t(q) * a.k_max + i] = ok ? uint32_t(key & 0xFFFFFFFFu) : 0xFFFFFFFFu;
             if (a.out_scores)
@@ -280,20 +399,19 @@ k_query(QArgs a)
     }
 }
 
-__global__ void __launch_bounds__(kQW * 32)
+__global__ void __launch_bounds__(kQT)
 k_counts(QArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
-    const QSmem s = carve_q(sm, a.cw, a.BR);
+    const QSmem s = carve_q(sm, a.cap, a.kp);
     const uint8_t *cnt8 = reinterpret_cast<const uint8_t *>(s.cntw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const uint32_t nwords = (a.BR + 3) / 4;
     for (uint32_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
-        for (uint32_t i = tid; i < nwords; i += kQW * 32) s.cntw[i] = 0u;
+        for (uint32_t i = tid; i < nwords; i += kQT) s.cntw[i] = 0u;
         __syncthreads();
-        gather_counts(a, s, q, lane, warp);
-        __syncthreads();
-        for (uint32_t c = tid; c < a.BR; c += kQW * 32) a.out_counts[size_t(q) * a.BR + c] = cnt8[c];
+        gather_counts(a, s, q);
+        for (uint32_t c = tid; c < a.BR; c += kQT) a.out_counts[size_t(q) * a.BR + c] = cnt8[c];
         __syncthreads();
     }
 }
@@ -329,7 +447,7 @@ int launch_query_rp(const QArgs &a, size_t smem, cudaStream_t st)
 {
     if (smem > 48 * 1024)
         FL_CUDA(cudaFuncSetAttribute(k_query<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_query<RP><<<a.nq, kQW * 32, smem, st>>>(a);
+    k_query<RP><<<a.nq, kQT, smem, st>>>(a);
     count_launch();
     FL_CUDA(cudaGetLastError());
     return FLINNG_OK;
@@ -345,11 +463,17 @@ int query_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
     QArgs a = make_args(ix, qbuckets, nq);
     a.k = k;
     a.k_max = k_max;
-    a.cw = pow2_at_least(k_max + 32 > 64 ? k_max + 32 : 64);
+    a.kp = pow2_at_least(k_max > 1 ? k_max : 2);
+    // room for one full round of members after a compaction to k keys
+    a.cap = pow2_at_least(a.kp + 2 * kQT > 2048 ? a.kp + 2 * kQT : 2048);
     a.out_ids = out_ids;
     a.out_scores = out_scores;
-    const size_t smem = qsmem_bytes(a.cw, a.BR, a.B);
-    if (smem > 227 * 1024)
+    size_t smem = qsmem_bytes(a.cap, a.kp, a.BR, a.B);
+    while (smem > 227 * 1024 && a.cap > a.kp + kQT) {       // large B*R: trade buffer for room
+        a.cap >>= 1;
+        smem = qsmem_bytes(a.cap, a.kp, a.BR, a.B);
+    }
+    if (smem > 227 * 1024 || a.cap < a.kp + kQT)
         return set_error(FLINNG_ERR_INVALID_ARG,
                          "query: k_max=%u with B*R=%u needs %zu bytes of shared memory (> 227 KB)",
                          k_max, a.BR, smem);
@@ -366,12 +490,13 @@ int counts_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
 {
     if (nq == 0) return FLINNG_OK;
     QArgs a = make_args(ix, qbuckets, nq);
-    a.cw = 1;
+    a.cap = 2;
+    a.kp = 2;
     a.out_counts = out_counts;
-    const size_t smem = qsmem_bytes(a.cw, a.BR, a.B);
+    const size_t smem = qsmem_bytes(a.cap, a.kp, a.BR, a.B);
     if (smem > 48 * 1024)
         FL_CUDA(cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_counts<<<nq, kQW * 32, smem, ix->stream>>>(a);
+    k_counts<<<nq, kQT, smem, ix->stream>>>(a);
     count_launch();
     FL_CUDA(cudaGetLastError());
     return FLINNG_OK;
