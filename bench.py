@@ -254,8 +254,8 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
-    path = os.path.join(ROOT, "profiles", f"k_query_{workload}_traffic.txt")
+def recorded_traffic(workload: str, kernel: str = "k_query_fused"):
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}_traffic.txt")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -351,29 +351,36 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
         if it >= 2:
             build_ms.append(e0.elapsed_time(e1))
 
-    # ---- staged buffers for the query step
+    # ---- query buffers (device)
     qb = torch.empty((nq, L), dtype=torch.int32, device=dev)
     ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
     sc = torch.empty((nq, k), dtype=torch.uint8, device=dev)
+    p_ids = torch.empty_like(ids)
+    p_sc = torch.empty_like(sc)
     fp, n_, devflag, keep = ix._points(d_q)
     import ctypes as C
     lib = ix.lib
 
-    def step():
+    def step_fused():
+        # the fused form (F2): one persistent kernel per batch
+        F._check(lib.flinng_query(ix.h, C.byref(fp), nq, None, k, ids.data_ptr(), sc.data_ptr(), 1))
+
+    def step_plain(e_mid):
+        # the plain form: hash kernel, then count/decode/top-k kernel
         F._check(lib.flinng_hash(ix.h, C.byref(fp), nq, qb.data_ptr(), None, None, 1))
         e_mid.record(stream)
-        F._check(lib.flinng_query_buckets(ix.h, qb.data_ptr(), nq, None, k, ids.data_ptr(),
-                                          sc.data_ptr(), 1))
+        F._check(lib.flinng_query_buckets(ix.h, qb.data_ptr(), nq, None, k, p_ids.data_ptr(),
+                                          p_sc.data_ptr(), 1))
 
-    # consistency: the staged step equals the single flinng_query call
-    e_mid = torch.cuda.Event(enable_timing=True)
-    step()
-    ids_q, sc_q = ix.query(d_q, k)
+    # the fused form: autotuned launch shape, CUDA graph per batch-size class
+    tuning = ix.tune(d_q, k)
+    ix.set_query_mode(F.QUERY_GRAPH)
+    # the two forms return the same results
+    step_fused()
+    step_plain(torch.cuda.Event(enable_timing=True))
     torch.cuda.synchronize()
-    assert torch.equal(ids, ids_q) and torch.equal(sc, sc_q), "staged step != flinng_query"
+    assert torch.equal(ids, p_ids) and torch.equal(sc, p_sc), "fused form != plain form"
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(dev.index)
     time.sleep(0.3)                                  # nvidia-smi start-up
     # warm-up: at least W steps, and at least 0.5 s of back-to-back steps so
@@ -382,7 +389,7 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     it = 0
     while it < args.warmup or time.time() - t_load < 0.5:
         flush.fill_(it)
-        step()
+        step_fused()
         if it % 50 == 0:
             torch.cuda.synchronize()
         it += 1
@@ -390,22 +397,21 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
     launches0 = F.kernel_launches()
     for it in range(args.steps):
         flush.fill_(it + 1)                         # evict L2 between steps (not timed)
-        e0, e_mid, e1 = ev[it]
+        e0, e1 = ev[it]
         e0.record(stream)
-        step()
+        step_fused()
         e1.record(stream)
     torch.cuda.synchronize()
     launches = F.kernel_launches() - launches0
     t_end = time.time()
     if dist is not None:
         dist.barrier()
-    clk = clocks.stop(t_load, t_end)
-    step_ms = [a.elapsed_time(b) for a, _, b in ev]
-    hash_ms = [a.elapsed_time(m) for a, m, _ in ev]
-    query_ms = [m.elapsed_time(b) for _, m, b in ev]
+    step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
     if dist is not None:
         t = torch.tensor([total_ms], device=dev)
@@ -413,6 +419,26 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     value = world * nq * args.steps / (total_ms / 1e3)
+
+    # ---- the plain form, same batch, per-stage events
+    for it in range(args.warmup):
+        flush.fill_(it)
+        step_plain(torch.cuda.Event(enable_timing=True))
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for it in range(args.steps):
+        flush.fill_(it + 1)
+        e0, em, e1 = pev[it]
+        e0.record(stream)
+        step_plain(em)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    t_end2 = time.time()
+    clk = clocks.stop(t_load, max(t_end, t_end2))
+    hash_ms = [a.elapsed_time(m) for a, m, _ in pev]
+    query_ms = [m.elapsed_time(b) for _, m, b in pev]
+    plain_ms = [a.elapsed_time(b) for a, _, b in pev]
+    plain_value = world * nq / (statistics.mean(plain_ms) / 1e3)
 
     # ---- e2e: flinng_query with host (pinned) buffers, copies inside the call
     if c["metric"] == "cosine":
@@ -461,11 +487,12 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     q_mean = statistics.mean(query_ms)
     h_mean = statistics.mean(hash_ms)
-    dom = "k_query" if q_mean >= h_mean else ("k_doph" if c["metric"] != "cosine" else "k_srp_fp32")
-    dom_bytes = qbytes["bytes"] if dom == "k_query" else hbytes
-    dom_ms = q_mean if dom == "k_query" else h_mean
+    # dominant kernel of the timed (fused) step: the fused kernel itself
+    dom = "k_query_fused"
+    dom_bytes = qbytes["bytes"] + hbytes
+    dom_ms = ms_per_step if world == 1 else statistics.mean(step_ms)
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
-    traffic = recorded_traffic(args.workload) if dom == "k_query" else None
+    traffic = recorded_traffic(args.workload)
     sorted_ms = sorted(step_ms)
 
     def pct(p):
@@ -476,20 +503,26 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32" if c["metric"] != "cosine" else "f32",
         "data": "synthetic (seeded; stands in for the paper's datasets)",
-        "config": {"workload": f"{args.workload}: {c['desc']}", "form": "plain batched",
+        "config": {"workload": f"{args.workload}: {c['desc']}",
+                   "form": "fused: one persistent kernel per batch (hash, gather, decode, top-k), "
+                           "CUDA graph per batch-size class, autotuned launch shape",
+                   "tuning": tuning,
                    "global_batch": world * nq, "k": k, "l2": "flushed before every step (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "recall": rec,
         "recall_target_met": rec["recall_at_10"] >= 0.9,
         "latency_ms": {"batch_p50": pct(50), "batch_p99": pct(99),
                        "note": "plain batched form: every query of a batch completes with the batch"},
-        "stages_ms": {"hash": h_mean, "query": q_mean},
+        "plain_form": {"value": plain_value, "unit": UNIT, "ms_per_step": statistics.mean(plain_ms),
+                       "stages_ms": {"hash": h_mean, "count_decode_topk": q_mean},
+                       "kernels": "k_doph|k_srp_fp32+k_srp_recheck, then k_query"},
         "build": {"ms": statistics.mean(build_ms), "points_per_s": c["N"] / (statistics.mean(build_ms) / 1e3),
                   "n_cells": int(ex["off"][-1])},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
                      "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": dom_bytes,
                      "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
+                     "algorithmic_bytes": "query hashing + per-query lists, enumerated members, outputs",
                      "members_enumerated_per_query": qbytes["members"] / nq},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "api": "flinng_query, host pinned buffers"},

@@ -161,6 +161,28 @@ uint64_t flinng_device_bytes(const flinng_index *idx);
 /* Set the stream used by subsequent calls (cudaStream_t or NULL). */
 int flinng_set_stream(flinng_index *idx, void *stream);
 
+/* How flinng_query runs a batch (same results in every mode):
+ * FLINNG_QUERY_PLAIN - a hash kernel for the batch, then one count / decode /
+ *   top-k kernel (one CTA per query);
+ * FLINNG_QUERY_FUSED - one persistent kernel that hashes each query in its
+ *   CTA and goes straight on to count / decode / top-k (default);
+ * FLINNG_QUERY_GRAPH - the fused kernel launched through a CUDA graph kept
+ *   per batch-size class (nq rounded up to a power of two); each call
+ *   rewrites the graph's kernel arguments and replays it. */
+#define FLINNG_QUERY_PLAIN 0
+#define FLINNG_QUERY_FUSED 1
+#define FLINNG_QUERY_GRAPH 2
+int flinng_set_query_mode(flinng_index *idx, uint32_t mode);
+
+/* Autotune the fused query on a sample batch: times CTA sizes (128, 256),
+ * CTAs per SM and candidate-buffer sizes on this batch (synchronously) and
+ * keeps the fastest for batches of the same size class (power of two of
+ * nq); later fused/graph calls of that class use it. Results never depend on
+ * the tuning. chosen (optional, 3 entries): threads, CTAs per SM (0 = as many
+ * as fit), buffer entries (0 = default). */
+int flinng_tune_query(flinng_index *idx, const flinng_points *q, uint32_t nq,
+                      uint32_t k_max, int on_device, uint32_t *chosen);
+
 /* ---------------------------------------------------------------------- */
 /* Stage entry points, for parity checks of each step against a reference */
 /* ---------------------------------------------------------------------- */

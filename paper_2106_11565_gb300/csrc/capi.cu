@@ -64,6 +64,7 @@ int dalloc(flinng_index *ix, T **p, size_t n)
 void free_index(flinng_index *ix)
 {
     if (!ix) return;
+    destroy_graphs(ix);
     void *ptrs[] = {ix->srp_w, ix->bucket_a, ix->bucket_c, ix->gid, ix->moff, ix->mem, ix->off,
                     ix->cells, ix->cells_tmp, ix->slot_a, ix->slot_b, ix->cell_cnt, ix->flag,
                     ix->stats, ix->ws.ptr};
@@ -243,8 +244,7 @@ int flinng_create(const flinng_config *cfg, const flinng_params *params, void *s
     if (!out) return set_error(FLINNG_ERR_INVALID_ARG, "create: out is null");
     *out = nullptr;
     FL_TRY(check_config(cfg, params));
-    flinng_index *ix = new flinng_index();
-    std::memset((void *)ix, 0, sizeof(*ix));
+    flinng_index *ix = new flinng_index();   // value-initialised: null pointers, zero counters
     ix->cfg = *cfg;
     ix->stream = (cudaStream_t)stream;
     cudaGetDevice(&ix->device);
@@ -254,6 +254,7 @@ int flinng_create(const flinng_config *cfg, const flinng_params *params, void *s
     ix->BR = cfg->B * R;
     ix->nslot = uint64_t(L) << cfg->range_bits;
     ix->entries_cap = uint64_t(L) * R * cfg->capacity;
+    ix->query_mode = FLINNG_QUERY_FUSED;
     int rc = FLINNG_OK;
 #define ALLOC(ptr, n)                                      \
     if (rc == FLINNG_OK) rc = dalloc(ix, &ix->ptr, (n));
@@ -334,6 +335,77 @@ int flinng_set_stream(flinng_index *idx, void *stream)
     return FLINNG_OK;
 }
 
+int flinng_set_query_mode(flinng_index *idx, uint32_t mode)
+{
+    if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
+    if (mode != FLINNG_QUERY_PLAIN && mode != FLINNG_QUERY_FUSED && mode != FLINNG_QUERY_GRAPH)
+        return set_error(FLINNG_ERR_INVALID_ARG, "unknown query mode %u", mode);
+    idx->query_mode = mode;
+    return FLINNG_OK;
+}
+
+int flinng_tune_query(flinng_index *idx, const flinng_points *q, uint32_t nq, uint32_t k_max,
+                      int on_device, uint32_t *chosen)
+{
+    if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
+    if (nq == 0) return set_error(FLINNG_ERR_INVALID_ARG, "tune: empty batch");
+    if (k_max > kMaxKMax) return set_error(FLINNG_ERR_INVALID_ARG, "tune: k_max > %u", kMaxKMax);
+    FL_TRY(check_points(idx, q, nq, on_device));
+    const cudaStream_t st = idx->stream;
+    const size_t need = 4096 + stage_bytes(idx, q, nq, on_device) + carve_bytes<uint32_t>(uint64_t(nq) * k_max) +
+                        carve_bytes<uint8_t>(uint64_t(nq) * k_max);
+    FL_TRY(ws_reserve(idx, need));
+    Carver c(idx->ws.ptr, idx->ws.bytes);
+    Staged fs;
+    FL_TRY(stage_points(idx, q, nq, on_device, c, fs));
+    uint32_t *ids = c.take<uint32_t>(uint64_t(nq) * k_max);
+    uint8_t *sc = c.take<uint8_t>(uint64_t(nq) * k_max);
+    FusedQuery fq{nq, fs.x, fs.ld, fs.off, fs.elems};
+    cudaEvent_t e0, e1;
+    FL_CUDA(cudaEventCreate(&e0));
+    FL_CUDA(cudaEventCreate(&e1));
+    QueryTuning best{};
+    float best_ms = 1e30f;
+    const uint32_t threads[] = {256, 128};
+    const uint32_t cps[] = {0, 4, 2};
+    const uint32_t caps[] = {0, 4096, 1024};
+    int rc = FLINNG_OK;
+    for (uint32_t th : threads)
+        for (uint32_t cp : cps)
+            for (uint32_t cap : caps) {
+                if (rc != FLINNG_OK) break;
+                QueryTuning t{th, cp, cap, 1};
+                rc = query_fused_launch(idx, fq, nullptr, k_max, ids, sc, &t);
+                if (rc != FLINNG_OK) break;
+                float ms_min = 1e30f;
+                for (int rep = 0; rep < 3 && rc == FLINNG_OK; ++rep) {
+                    cudaEventRecord(e0, st);
+                    rc = query_fused_launch(idx, fq, nullptr, k_max, ids, sc, &t);
+                    cudaEventRecord(e1, st);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) rc = cuda_error(cudaGetLastError(), "tune sync");
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < ms_min) ms_min = ms;
+                }
+                if (ms_min < best_ms) {
+                    best_ms = ms_min;
+                    best = t;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != FLINNG_OK) return rc;
+    uint32_t bucket = 0;
+    while ((1u << bucket) < nq) ++bucket;
+    idx->tuning[bucket] = best;
+    if (chosen) {
+        chosen[0] = best.threads;
+        chosen[1] = best.ctas_per_sm;
+        chosen[2] = best.cap;
+    }
+    return FLINNG_OK;
+}
+
 int flinng_build(flinng_index *idx, const flinng_points *pts, uint64_t n, const uint32_t *perm,
                  int on_device)
 {
@@ -406,8 +478,12 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
                 carve_bytes<uint8_t>(uint64_t(nq) * k_max);
     FL_TRY(ws_reserve(idx, need));
     Carver c(idx->ws.ptr, idx->ws.bytes);
-    uint32_t *qb;
-    if (q) {
+    uint32_t *qb = nullptr;
+    const bool fused = q && (idx->query_mode == FLINNG_QUERY_FUSED || idx->query_mode == FLINNG_QUERY_GRAPH);
+    Staged fs;
+    if (fused) {
+        FL_TRY(stage_points(idx, q, nq, on_device, c, fs));
+    } else if (q) {
         Staged s;
         FL_TRY(stage_points(idx, q, nq, on_device, c, s));
         qb = c.take<uint32_t>(uint64_t(nq) * L);
@@ -432,7 +508,19 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
         dids = c.take<uint32_t>(uint64_t(nq) * k_max);
         dsc = out_scores ? c.take<uint8_t>(uint64_t(nq) * k_max) : nullptr;
     }
-    FL_TRY(query_launch(idx, qb, nq, dk, k_max, dids, dsc));
+    if (fused) {
+        FusedQuery fq{nq, fs.x, fs.ld, fs.off, fs.elems};
+        const QueryTuning *tune = nullptr;
+        uint32_t bucket = 0;
+        while ((1u << bucket) < nq) ++bucket;
+        if (idx->tuning[bucket].valid) tune = &idx->tuning[bucket];
+        if (idx->query_mode == FLINNG_QUERY_GRAPH)
+            FL_TRY(query_graph_launch(idx, fq, dk, k_max, dids, dsc, tune));
+        else
+            FL_TRY(query_fused_launch(idx, fq, dk, k_max, dids, dsc, tune));
+    } else {
+        FL_TRY(query_launch(idx, qb, nq, dk, k_max, dids, dsc));
+    }
     if (!on_device) {
         if (k_max) {
             FL_CUDA(cudaMemcpyAsync(out_ids, dids, uint64_t(nq) * k_max * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));

@@ -37,6 +37,22 @@ struct Workspace {
     size_t bytes = 0;
 };
 
+struct QueryTuning {
+    uint32_t threads;        // CTA size: 128 or 256 (0: 256)
+    uint32_t ctas_per_sm;    // 0: occupancy limit
+    uint32_t cap;            // candidate buffer entries; 0: default
+    uint32_t valid;
+};
+
+struct QueryGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t node = nullptr;
+    const void *fn = nullptr;
+    size_t smem = 0;
+    uint32_t grid = 0;
+};
+
 // Bump allocator over a workspace, 256-byte aligned slices.
 struct Carver {
     char *base;
@@ -95,6 +111,9 @@ struct flinng_index {
 
     flinng::Workspace ws;
     uint64_t device_bytes;
+    uint32_t query_mode;   // FLINNG_QUERY_PLAIN, _FUSED or _GRAPH
+    flinng::QueryTuning tuning[33];   // per batch-size class (ceil log2 nq)
+    flinng::QueryGraph graphs[33];
 };
 
 namespace flinng {
@@ -127,6 +146,18 @@ int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *per
                   uint64_t n, void *ws);
 
 // ---- query.cu
+struct FusedQuery {
+    uint32_t nq;
+    const float *x;          // cosine: device rows
+    uint64_t ldx;
+    const uint64_t *off;     // Jaccard: device CSR
+    const uint32_t *elems;
+};
+int query_fused_launch(flinng_index *ix, const FusedQuery &fq, const uint32_t *k, uint32_t k_max,
+                       uint32_t *out_ids, uint8_t *out_scores, const QueryTuning *tune);
+int query_graph_launch(flinng_index *ix, const FusedQuery &fq, const uint32_t *k, uint32_t k_max,
+                       uint32_t *out_ids, uint8_t *out_scores, const QueryTuning *tune);
+void destroy_graphs(flinng_index *ix);
 int query_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
                  const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
                  uint8_t *out_scores);

@@ -30,8 +30,7 @@ namespace flinng {
 
 namespace {
 
-constexpr int kQT = 256;                 // threads per query CTA
-constexpr int kQW = kQT / 32;
+constexpr int kQTmax = 256;              // largest CTA size (threads) of the query kernels
 constexpr uint64_t kKeyBits = (1ull << 56) - 1;
 
 struct QArgs {
@@ -60,22 +59,23 @@ struct QSmem {
     uint32_t *lvl_n;     // 256: repetition-0 cells per count
     uint32_t *lvl_cur;   // 256
     uint32_t *rhist;     // 256: radix histogram
-    uint32_t *c_start;   // kQT: member start of each cell of a chunk / list start
-    uint32_t *c_pre;     // kQT + 1: exclusive prefix of member counts
-    uint32_t *wsum;      // kQW: block-scan scratch
+    uint32_t *c_start;   // NT: member start of each cell of a chunk / list start
+    uint32_t *c_pre;     // NT + 1: exclusive prefix of member counts
+    uint32_t *wsum;      // NT / 32: block-scan scratch
     uint32_t *cntw;      // (BR + 3) / 4 words of byte counts
     uint16_t *lvl_cells; // B
 };
 
-__host__ __device__ inline size_t qsmem_bytes(uint32_t cap, uint32_t kp, uint32_t BR, uint32_t B)
+__host__ __device__ inline size_t qsmem_bytes(uint32_t cap, uint32_t kp, uint32_t BR, uint32_t B, int NT)
 {
-    size_t b = size_t(cap) * 8 + size_t(kp) * 8 + 8 * 4 + 4 * 256 * 4 + kQT * 4 + (kQT + 1) * 4 + kQW * 4;
+    size_t b = size_t(cap) * 8 + size_t(kp) * 8 + 8 * 4 + 4 * 256 * 4 + NT * 4 + (NT + 1) * 4 + (NT / 32) * 4;
     b = (b + 15) & ~size_t(15);
     b += size_t((BR + 3) / 4) * 4;
     b += size_t(B) * 2;
     return (b + 15) & ~size_t(15);
 }
 
+template <int NT>
 __device__ inline QSmem carve_q(unsigned char *sm, uint32_t cap, uint32_t kp)
 {
     QSmem s;
@@ -87,9 +87,9 @@ __device__ inline QSmem carve_q(unsigned char *sm, uint32_t cap, uint32_t kp)
     s.lvl_cur = s.lvl_n + 256;
     s.rhist = s.lvl_cur + 256;
     s.c_start = s.rhist + 256;
-    s.c_pre = s.c_start + kQT;
-    s.wsum = s.c_pre + kQT + 1;
-    size_t o = (size_t)((unsigned char *)(s.wsum + kQW) - sm);
+    s.c_pre = s.c_start + NT;
+    s.wsum = s.c_pre + NT + 1;
+    size_t o = (size_t)((unsigned char *)(s.wsum + NT / 32) - sm);
     o = (o + 15) & ~size_t(15);
     s.cntw = (uint32_t *)(sm + o);
     return s;
@@ -121,6 +121,7 @@ __device__ inline void load_gid(const uint16_t *__restrict__ gid, uint32_t x, ui
 
 // Exclusive block scan of one value per thread; returns the prefix and
 // writes the total to *total (all threads). Contains __syncthreads.
+template <int NT>
 __device__ uint32_t block_excl_scan(uint32_t v, uint32_t *wsum, uint32_t *total)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -134,7 +135,7 @@ __device__ uint32_t block_excl_scan(uint32_t v, uint32_t *wsum, uint32_t *total)
     __syncthreads();
     uint32_t before = 0, all = 0;
 #pragma unroll
-    for (int w = 0; w < kQW; ++w) {
+    for (int w = 0; w < NT / 32; ++w) {
         const uint32_t t = wsum[w];
         before += (w < warp) ? t : 0u;
         all += t;
@@ -158,6 +159,7 @@ __device__ inline uint32_t find_seg(const uint32_t *pre, uint32_t n, uint32_t j)
 
 // Radix select over keys[0..n): returns (prefix, mask) such that exactly kk
 // keys satisfy (key & mask) <= prefix (keys are unique, kk <= n).
+template <int NT>
 __device__ void block_select(const uint64_t *keys, uint32_t n, uint32_t kk, const QSmem &s,
                              uint64_t &prefix_out, uint64_t &mask_out)
 {
@@ -165,9 +167,9 @@ __device__ void block_select(const uint64_t *keys, uint32_t n, uint32_t kk, cons
     uint64_t prefix = 0, mask = 0;
     uint32_t rem = kk;
     for (int shift = 48; shift >= 0; shift -= 8) {
-        s.rhist[tid] = 0u;                      // kQT == 256 bins
+        for (int i = tid; i < 256; i += NT) s.rhist[i] = 0u;
         __syncthreads();
-        for (uint32_t i = tid; i < n; i += kQT) {
+        for (uint32_t i = tid; i < n; i += NT) {
             const uint64_t v = keys[i];
             if ((v & mask) == prefix) atomicAdd(&s.rhist[(v >> shift) & 0xFF], 1u);
         }
@@ -221,44 +223,44 @@ __device__ void block_select(const uint64_t *keys, uint32_t n, uint32_t kk, cons
 
 // Keep the kk best of buf[0..nbuf) in buf[0..kk); returns the new admission
 // bound (keys above it can never enter the top kk).
+template <int NT>
 __device__ uint64_t block_compact(const QSmem &s, uint32_t nbuf, uint32_t kk)
 {
     uint64_t prefix, mask;
-    block_select(s.buf, nbuf, kk, s, prefix, mask);
+    block_select<NT>(s.buf, nbuf, kk, s, prefix, mask);
     if (threadIdx.x == 0) s.u[1] = 0u;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nbuf; i += kQT) {
+    for (uint32_t i = threadIdx.x; i < nbuf; i += NT) {
         const uint64_t v = s.buf[i];
         if ((v & mask) <= prefix) s.keep[atomicAdd(&s.u[1], 1u)] = v;
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < kk; i += kQT) s.buf[i] = s.keep[i];
+    for (uint32_t i = threadIdx.x; i < kk; i += NT) s.buf[i] = s.keep[i];
     if (threadIdx.x == 0) s.u[0] = kk;
     __syncthreads();
     return prefix | (~mask & kKeyBits);
 }
 
-__device__ void gather_counts(const QArgs &a, const QSmem &s, uint32_t q)
+template <int NT>
+__device__ void gather_counts(const QArgs &a, const QSmem &s, const uint32_t *qb)
 {
     const int tid = threadIdx.x;
     // one thread per table: its list's start and length
-    uint32_t len = 0;
-    for (uint32_t l0 = 0; l0 < a.L; l0 += kQT) {
+    for (uint32_t l0 = 0; l0 < a.L; l0 += NT) {
         const uint32_t l = l0 + tid;
-        uint32_t beg = 0;
-        len = 0;
+        uint32_t beg = 0, len = 0;
         if (l < a.L) {
-            const uint64_t slot = (uint64_t(l) << a.W) | a.qb[size_t(q) * a.L + l];
+            const uint64_t slot = (uint64_t(l) << a.W) | qb[l];
             beg = a.off[slot];
             len = a.off[slot + 1] - beg;
         }
         uint32_t total;
-        const uint32_t pre = block_excl_scan(len, s.wsum, &total);
+        const uint32_t pre = block_excl_scan<NT>(len, s.wsum, &total);
         s.c_start[tid] = beg;
         s.c_pre[tid] = pre;
         __syncthreads();
-        const uint32_t nl = min(uint32_t(kQT), a.L - l0);
-        for (uint32_t e = tid; e < total; e += kQT) {
+        const uint32_t nl = min(uint32_t(NT), a.L - l0);
+        for (uint32_t e = tid; e < total; e += NT) {
             const uint32_t t = find_seg(s.c_pre, nl, e);
             const uint32_t c = a.cells[s.c_start[t] + (e - s.c_pre[t])];
             atomicAdd(&s.cntw[c >> 2], 1u << ((c & 3) * 8));
@@ -267,151 +269,380 @@ __device__ void gather_counts(const QArgs &a, const QSmem &s, uint32_t q)
     }
 }
 
-template <int RP>
-__global__ void __launch_bounds__(kQT)
-k_query(QArgs a)
+template <int NT>
+__device__ inline void zero_query_state(const QArgs &a, const QSmem &s)
 {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const QSmem s = carve_q(sm, a.cap, a.kp);
+    const int tid = threadIdx.x;
+    const uint32_t nwords = (a.BR + 3) / 4;
+    for (uint32_t i = tid; i < nwords; i += NT) s.cntw[i] = 0u;
+    for (int i = tid; i < 256; i += NT) {
+        s.hist_s[i] = 0u;
+        s.lvl_n[i] = 0u;
+    }
+    if (tid < 8) s.u[tid] = 0u;
+}
+
+// Group tests, AND-over-R decode and top-k of query q, from the counts in
+// shared memory; writes row q of the outputs.
+template <int NT, int RP>
+__device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t kq)
+{
     uint16_t *lvl_cells = lvl_cells_ptr(s, a.BR);
     const uint8_t *cnt8 = reinterpret_cast<const uint8_t *>(s.cntw);
     const int tid = threadIdx.x;
-    const uint32_t nwords = (a.BR + 3) / 4;
+    if (kq > 0) {
+        // group tests of repetition 0, bucketed by count level
+        for (uint32_t b = tid; b < a.B; b += NT) {
+            const uint32_t v = cnt8[b];
+            if (v >= a.t_min) atomicAdd(&s.lvl_n[v], 1u);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t run = 0;
+            for (int t = int(a.L); t >= int(a.t_min); --t) {
+                s.lvl_cur[t] = run;
+                run += s.lvl_n[t];
+            }
+        }
+        __syncthreads();
+        for (uint32_t b = tid; b < a.B; b += NT) {
+            const uint32_t v = cnt8[b];
+            if (v >= a.t_min) lvl_cells[atomicAdd(&s.lvl_cur[v], 1u)] = uint16_t(b);
+        }
+        __syncthreads();
+        // decode, level by level
+        uint64_t bound = kKeyBits;           // admission: key <= bound
+        uint32_t seen = 0;                   // points with score >= current level
+        const uint32_t sub = a.cap - a.kp;   // members per round (room after a compaction)
+        for (int t = int(a.L); t >= int(a.t_min); --t) {
+            const uint32_t nc = s.lvl_n[t];
+            const uint32_t first = s.lvl_cur[t] - nc;
+            for (uint32_t c0 = 0; c0 < nc; c0 += NT) {
+                const uint32_t ci = c0 + tid;
+                uint32_t ms = 0, sz = 0;
+                if (ci < nc) {
+                    const uint32_t b = lvl_cells[first + ci];
+                    ms = a.moff[b];
+                    sz = a.moff[b + 1] - ms;
+                }
+                uint32_t M;
+                const uint32_t pre = block_excl_scan<NT>(sz, s.wsum, &M);
+                s.c_start[tid] = ms;
+                s.c_pre[tid] = pre;
+                const uint32_t ncc = min(uint32_t(NT), nc - c0);
+                __syncthreads();
+                for (uint32_t j0 = 0; j0 < M; j0 += sub) {
+                    const uint32_t jn = min(M, j0 + sub);
+                    if (s.u[0] + (jn - j0) > a.cap) bound = block_compact<NT>(s, s.u[0], kq);
+                    for (uint32_t j = j0 + tid; j < jn; j += NT) {
+                        const uint32_t cs = find_seg(s.c_pre, ncc, j);
+                        const uint32_t x = __ldg(a.mem + s.c_start[cs] + (j - s.c_pre[cs]));
+                        uint32_t g[RP];
+                        load_gid<RP>(a.gid, x, g);
+                        uint32_t score = 256, last = 0;
+#pragma unroll
+                        for (int r = 0; r < RP; ++r) {
+                            if (r < int(a.R)) {
+                                const uint32_t c = uint32_t(r) * a.B + g[r];
+                                const uint32_t v = cnt8[c];
+                                if (v < score) {
+                                    score = v;
+                                    last = c;
+                                } else if (v == score) {
+                                    last = c;
+                                }
+                            }
+                        }
+                        if (score >= a.t_min) {
+                            atomicAdd(&s.hist_s[score], 1u);
+                            const uint64_t key = (uint64_t(255u - score) << 48) | (uint64_t(last) << 32) | x;
+                            if (key <= bound) s.buf[atomicAdd(&s.u[0], 1u)] = key;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            seen += s.hist_s[t];             // final: later levels only add scores < t
+            if (seen >= kq) break;
+        }
+    }
+    __syncthreads();
+    // final top-k: cut to kq keys, sort, write
+    const uint32_t nbuf = s.u[0];
+    const uint32_t nk = nbuf < kq ? nbuf : kq;
+    if (nbuf > kq) block_compact<NT>(s, nbuf, kq);
+    for (uint32_t i = tid; i < a.kp; i += NT) s.keep[i] = (i < nk) ? s.buf[i] : kKeyNone;
+    __syncthreads();
+    for (uint32_t k2 = 2; k2 <= a.kp; k2 <<= 1) {
+        for (uint32_t j = k2 >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = tid; i < a.kp; i += NT) {
+                const uint32_t l = i ^ j;
+                if (l > i) {
+                    const uint64_t x = s.keep[i], y = s.keep[l];
+                    const bool up = (i & k2) == 0;
+                    if ((x > y) == up) {
+                        s.keep[i] = y;
+                        s.keep[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (uint32_t i = tid; i < a.k_max; i += NT) {
+        const uint64_t key = (i < nk) ? s.keep[i] : kKeyNone;
+        const bool ok = key != kKeyNone;
+        a.out_ids[size_t(q) * a.k_max + i] = ok ? uint32_t(key & 0xFFFFFFFFu) : 0xFFFFFFFFu;
+        if (a.out_scores)
+            a.out_scores[size_t(q) * a.k_max + i] = ok ? uint8_t(255u - uint32_t(key >> 48)) : uint8_t(0);
+    }
+    __syncthreads();
+}
 
+template <int NT, int RP>
+__global__ void __launch_bounds__(NT, 2048 / NT)
+k_query(QArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    const QSmem s = carve_q<NT>(sm, a.cap, a.kp);
     for (uint32_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
         uint32_t kq = a.k ? a.k[q] : a.k_max;
         if (kq > a.k_max) kq = a.k_max;
-        for (uint32_t i = tid; i < nwords; i += kQT) s.cntw[i] = 0u;
-        s.hist_s[tid] = 0u;
-        s.lvl_n[tid] = 0u;
-        if (tid < 8) s.u[tid] = 0u;
+        zero_query_state<NT>(a, s);
         __syncthreads();
-        if (kq > 0) {
-            gather_counts(a, s, q);
-            // group tests of repetition 0, bucketed by count level
-            for (uint32_t b = tid; b < a.B; b += kQT) {
-                const uint32_t v = cnt8[b];
-                if (v >= a.t_min) atomicAdd(&s.lvl_n[v], 1u);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                uint32_t run = 0;
-                for (int t = int(a.L); t >= int(a.t_min); --t) {
-                    s.lvl_cur[t] = run;
-                    run += s.lvl_n[t];
-                }
-            }
-            __syncthreads();
-            for (uint32_t b = tid; b < a.B; b += kQT) {
-                const uint32_t v = cnt8[b];
-                if (v >= a.t_min) lvl_cells[atomicAdd(&s.lvl_cur[v], 1u)] = uint16_t(b);
-            }
-            __syncthreads();
-            // decode, level by level
-            uint64_t bound = kKeyBits;           // admission: key <= bound
-            uint32_t seen = 0;                   // points with score >= current level
-            const uint32_t sub = a.cap - a.kp;   // members per round (room after a compaction)
-            for (int t = int(a.L); t >= int(a.t_min); --t) {
-                const uint32_t nc = s.lvl_n[t];
-                const uint32_t first = s.lvl_cur[t] - nc;
-                for (uint32_t c0 = 0; c0 < nc; c0 += kQT) {
-                    const uint32_t ci = c0 + tid;
-                    uint32_t ms = 0, sz = 0;
-                    if (ci < nc) {
-                        const uint32_t b = lvl_cells[first + ci];
-                        ms = a.moff[b];
-                        sz = a.moff[b + 1] - ms;
-                    }
-                    uint32_t M;
-                    const uint32_t pre = block_excl_scan(sz, s.wsum, &M);
-                    s.c_start[tid] = ms;
-                    s.c_pre[tid] = pre;
-                    const uint32_t ncc = min(uint32_t(kQT), nc - c0);
-                    __syncthreads();
-                    for (uint32_t j0 = 0; j0 < M; j0 += sub) {
-                        const uint32_t jn = min(M, j0 + sub);
-                        if (s.u[0] + (jn - j0) > a.cap) bound = block_compact(s, s.u[0], kq);
-                        for (uint32_t j = j0 + tid; j < jn; j += kQT) {
-                            const uint32_t cs = find_seg(s.c_pre, ncc, j);
-                            const uint32_t x = __ldg(a.mem + s.c_start[cs] + (j - s.c_pre[cs]));
-                            uint32_t g[RP];
-                            load_gid<RP>(a.gid, x, g);
-                            uint32_t score = 256, last = 0;
-#pragma unroll
-                            for (int r = 0; r < RP; ++r) {
-                                if (r < int(a.R)) {
-                                    const uint32_t c = uint32_t(r) * a.B + g[r];
-                                    const uint32_t v = cnt8[c];
-                                    if (v < score) {
-                                        score = v;
-                                        last = c;
-                                    } else if (v == score) {
-                                        last = c;
-                                    }
-                                }
-                            }
-                            if (score >= a.t_min) {
-                                atomicAdd(&s.hist_s[score], 1u);
-                                const uint64_t key = (uint64_t(255u - score) << 48) | (uint64_t(last) << 32) | x;
-                                if (key <= bound) s.buf[atomicAdd(&s.u[0], 1u)] = key;
-                            }
-                        }
-                        __syncthreads();
-                    }
-                }
-                seen += s.hist_s[t];             // final: later levels only add scores < t
-                if (seen >= kq) break;
-            }
-        }
-        __syncthreads();
-        // final top-k: cut to kq keys, sort, write
-        const uint32_t nbuf = s.u[0];
-        const uint32_t nk = nbuf < kq ? nbuf : kq;
-        if (nbuf > kq) {
-            block_compact(s, nbuf, kq);
-        }
-        for (uint32_t i = tid; i < a.kp; i += kQT) s.keep[i] = (i < nk) ? s.buf[i] : kKeyNone;
-        __syncthreads();
-        for (uint32_t k2 = 2; k2 <= a.kp; k2 <<= 1) {
-            for (uint32_t j = k2 >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = tid; i < a.kp; i += kQT) {
-                    const uint32_t l = i ^ j;
-                    if (l > i) {
-                        const uint64_t x = s.keep[i], y = s.keep[l];
-                        const bool up = (i & k2) == 0;
-                        if ((x > y) == up) {
-                            s.keep[i] = y;
-                            s.keep[l] = x;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        for (uint32_t i = tid; i < a.k_max; i += kQT) {
-            const uint64_t key = (i < nk) ? s.keep[i] : kKeyNone;
-            const bool ok = key != kKeyNone;
-            a.out_ids[size_t(q) * a.k_max + i] = ok ? uint32_t(key & 0xFFFFFFFFu) : 0xFFFFFFFFu;
-            if (a.out_scores)
-                a.out_scores[size_t(q) * a.k_max + i] = ok ? uint8_t(255u - uint32_t(key >> 48)) : uint8_t(0);
-        }
-        __syncthreads();
+        if (kq > 0) gather_counts<NT>(a, s, a.qb + size_t(q) * a.L);
+        decode_topk<NT, RP>(a, s, q, kq);
     }
 }
 
-__global__ void __launch_bounds__(kQT)
-k_counts(QArgs a)
+// ---------------------------------------------------------------- fused form
+//
+// One launch for the whole batch: each CTA hashes its query in shared memory
+// (DOPH over the query's set, or the L*K sign projections of its vector),
+// then runs the same gather / decode / top-k. The grid is persistent: CTAs
+// loop over queries. The hashing follows the same definitions as the hash
+// kernels (hash.cu), the bucket results are identical.
+
+struct HArgs {
+    // Jaccard
+    const uint64_t *q_off;
+    const uint32_t *q_el;
+    uint32_t nb, da, db;
+    uint64_t seed;
+    const uint64_t *ba;
+    const uint64_t *bc;
+    // cosine
+    const float *x;
+    uint64_t ldx;
+    const float *w;
+    uint32_t d;
+    float gamma2, tiny;
+    double gamma64;
+    unsigned long long *stats;
+    uint32_t K;
+    size_t hash_off;    // byte offset of the hash region in shared memory
+};
+
+__device__ __forceinline__ uint64_t splitmix64_q(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// DOPH of query q into qb[0..L) (shared memory). Contains __syncthreads.
+template <int NT>
+__device__ void cta_doph(const QArgs &a, const HArgs &h, uint32_t q, uint32_t *qb, uint32_t *val)
+{
+    const int tid = threadIdx.x;
+    const uint32_t nb = h.nb;
+    uint32_t *occ = val + nb;
+    for (uint32_t k = tid; k < nb; k += NT) val[k] = kEmpty32;
+    for (uint32_t k = tid; k < (nb + 31) / 32; k += NT) occ[k] = 0u;
+    __syncthreads();
+    const uint64_t beg = h.q_off[q], end = h.q_off[q + 1];
+    for (uint64_t t = beg + tid; t < end; t += NT) {
+        const uint32_t pe = h.da * __ldg(h.q_el + t) + h.db;
+        const uint32_t bin = __umulhi(pe, nb);
+        atomicMin(&val[bin], pe);
+        atomicOr(&occ[bin >> 5], 1u << (bin & 31));
+    }
+    __syncthreads();
+    if (end > beg) {
+        for (uint32_t k = tid; k < nb; k += NT) {
+            if ((occ[k >> 5] >> (k & 31)) & 1u) continue;
+            bool found = false;
+            for (uint32_t att = 1; att <= kDophMaxAttempts; ++att) {
+                const uint32_t j = uint32_t(splitmix64_q(h.seed ^ ((uint64_t(k) << 32) | att)) % nb);
+                if ((occ[j >> 5] >> (j & 31)) & 1u) {
+                    val[k] = val[j];
+                    found = true;
+                    break;
+                }
+            }
+            if (!found) {
+                for (uint32_t s2 = 1; s2 <= nb; ++s2) {
+                    const uint32_t j = (k + s2) % nb;
+                    if ((occ[j >> 5] >> (j & 31)) & 1u) {
+                        val[k] = val[j];
+                        break;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t l = tid; l < a.L; l += NT) {
+        uint64_t hh = h.bc[l];
+        for (uint32_t j = 0; j < h.K; ++j) hh += h.ba[l * h.K + j] * uint64_t(val[l * h.K + j]);
+        qb[l] = uint32_t(hh >> (64 - a.W));
+    }
+    __syncthreads();
+}
+
+// Exact sign of sum_t a_t b_t for fp32 inputs, by one warp: fixed-point
+// digits of 32 bits from 2^-384 upward, summed over lanes in int64.
+__device__ int warp_exact_sign(const float *xa, const float *wb, uint32_t d, int lane)
+{
+    constexpr int kLimbs = 24;
+    long long acc[kLimbs + 2];
+    for (int i = 0; i < kLimbs + 2; ++i) acc[i] = 0;
+    for (uint32_t t = lane; t < d; t += 32) {
+        const double v = double(xa[t]) * double(wb[t]);
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+        const int ex = int((bits >> 52) & 0x7FF);
+        unsigned long long man = bits & ((1ull << 52) - 1);
+        if (ex == 0 && man == 0) continue;
+        int lsb;
+        if (ex == 0) {
+            lsb = 1 - 1075;
+        } else {
+            man |= 1ull << 52;
+            lsb = ex - 1075;
+        }
+        const int pos = lsb + 384;
+        const int qd = pos >> 5, r = pos & 31;
+        const unsigned long long d0 = (man << r) & 0xffffffffull;
+        const unsigned long long d1 = (r == 0 ? (man >> 32) : (man >> (32 - r))) & 0xffffffffull;
+        const unsigned long long d2 = (r == 0) ? 0ull : (man >> (64 - r));
+        const long long sg = (bits >> 63) ? -1 : 1;
+        acc[qd] += sg * (long long)d0;
+        acc[qd + 1] += sg * (long long)d1;
+        acc[qd + 2] += sg * (long long)d2;
+    }
+    for (int i = 0; i < kLimbs + 2; ++i) {
+        long long v = acc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        acc[i] = v;
+    }
+    acc[kLimbs - 1] += acc[kLimbs] * 4294967296ll;
+    for (int i = 0; i < kLimbs - 1; ++i) {
+        const long long c = acc[i] >> 32;
+        acc[i] -= c * 4294967296ll;
+        acc[i + 1] += c;
+    }
+    if (acc[kLimbs - 1] != 0) return acc[kLimbs - 1] > 0 ? 1 : -1;
+    for (int i = kLimbs - 2; i >= 0; --i)
+        if (acc[i] != 0) return 1;
+    return 0;
+}
+
+// SRP codes of query q into qb[0..L): one warp per projection, fp32 with a
+// rigorous error bound, fp64 re-check, exact accumulator last. Contains
+// __syncthreads.
+template <int NT>
+__device__ void cta_srp(const QArgs &a, const HArgs &h, uint32_t q, uint32_t *qb, float *xs)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float *xq = h.x + size_t(q) * h.ldx;
+    for (uint32_t t = tid; t < h.d; t += NT) xs[t] = xq[t];
+    for (uint32_t l = tid; l < a.L; l += NT) qb[l] = 0u;
+    __syncthreads();
+    const uint32_t P = a.L * h.K;
+    for (uint32_t j = warp; j < P; j += (NT / 32)) {
+        const float *wj = h.w + size_t(j) * h.d;
+        float p = 0.f, sa = 0.f;
+        for (uint32_t t = lane; t < h.d; t += 32) {
+            const float wv = __ldg(wj + t), xv = xs[t];
+            p = fmaf(wv, xv, p);
+            sa = fmaf(fabsf(wv), fabsf(xv), sa);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            p += __shfl_xor_sync(0xffffffffu, p, o);
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        }
+        p = __shfl_sync(0xffffffffu, p, 0);
+        sa = __shfl_sync(0xffffffffu, sa, 0);
+        bool positive;
+        if (fabsf(p) > fmaf(h.gamma2, sa, h.tiny)) {
+            positive = p > 0.f;
+        } else {
+            double p64 = 0.0, s64 = 0.0;
+            for (uint32_t t = lane; t < h.d; t += 32) {
+                const double prod = double(wj[t]) * double(xs[t]);
+                p64 += prod;
+                s64 += fabs(prod);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                p64 += __shfl_xor_sync(0xffffffffu, p64, o);
+                s64 += __shfl_xor_sync(0xffffffffu, s64, o);
+            }
+            p64 = __shfl_sync(0xffffffffu, p64, 0);
+            s64 = __shfl_sync(0xffffffffu, s64, 0);
+            if (fabs(p64) > h.gamma64 * s64) {
+                positive = p64 > 0.0;
+            } else {
+                positive = warp_exact_sign(xs, wj, h.d, lane) > 0;
+                if (lane == 0) atomicAdd(&h.stats[1], 1ull);
+            }
+            if (lane == 0) atomicAdd(&h.stats[0], 1ull);
+        }
+        if (lane == 0 && positive) atomicOr(&qb[j / h.K], 1u << (j % h.K));
+    }
+    __syncthreads();
+}
+
+template <int NT, int RP, int HASH>
+__global__ void __launch_bounds__(NT, (HASH == 2 ? 1024 : 2048) / NT)
+k_query_fused(QArgs a, HArgs h)
 {
     extern __shared__ __align__(16) unsigned char sm[];
-    const QSmem s = carve_q(sm, a.cap, a.kp);
+    const QSmem s = carve_q<NT>(sm, a.cap, a.kp);
+    uint32_t *qb = reinterpret_cast<uint32_t *>(sm + h.hash_off);
+    uint32_t *hs = qb + ((a.L + 3) & ~3u);
+    for (uint32_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
+        uint32_t kq = a.k ? a.k[q] : a.k_max;
+        if (kq > a.k_max) kq = a.k_max;
+        zero_query_state<NT>(a, s);
+        if (kq > 0) {
+            if constexpr (HASH == 1) cta_doph<NT>(a, h, q, qb, hs);
+            else cta_srp<NT>(a, h, q, qb, reinterpret_cast<float *>(hs));
+            gather_counts<NT>(a, s, qb);
+        } else {
+            __syncthreads();
+        }
+        decode_topk<NT, RP>(a, s, q, kq);
+    }
+}
+
+__global__ void __launch_bounds__(kQTmax)
+k_counts(QArgs a)
+{
+    constexpr int NT = kQTmax;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const QSmem s = carve_q<NT>(sm, a.cap, a.kp);
     const uint8_t *cnt8 = reinterpret_cast<const uint8_t *>(s.cntw);
     const int tid = threadIdx.x;
     const uint32_t nwords = (a.BR + 3) / 4;
     for (uint32_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
-        for (uint32_t i = tid; i < nwords; i += kQT) s.cntw[i] = 0u;
+        for (uint32_t i = tid; i < nwords; i += NT) s.cntw[i] = 0u;
         __syncthreads();
-        gather_counts(a, s, q);
-        for (uint32_t c = tid; c < a.BR; c += kQT) a.out_counts[size_t(q) * a.BR + c] = cnt8[c];
+        gather_counts<NT>(a, s, a.qb + size_t(q) * a.L);
+        for (uint32_t c = tid; c < a.BR; c += NT) a.out_counts[size_t(q) * a.BR + c] = cnt8[c];
         __syncthreads();
     }
 }
@@ -442,15 +673,47 @@ QArgs make_args(flinng_index *ix, const uint32_t *qb, uint32_t nq)
     return a;
 }
 
-template <int RP>
-int launch_query_rp(const QArgs &a, size_t smem, cudaStream_t st)
+// Candidate buffer: room for one full round of members after a compaction
+// to k keys; tune->cap overrides the default when large enough.
+void pick_buffer(QArgs &a, int NT, const QueryTuning *tune, size_t extra, size_t *smem_out)
 {
-    if (smem > 48 * 1024)
-        FL_CUDA(cudaFuncSetAttribute(k_query<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_query<RP><<<a.nq, kQT, smem, st>>>(a);
-    count_launch();
-    FL_CUDA(cudaGetLastError());
-    return FLINNG_OK;
+    a.kp = pow2_at_least(a.k_max > 1 ? a.k_max : 2);
+    const uint32_t cap_min = pow2_at_least(a.kp + 2 * NT);
+    uint32_t cap = (tune && tune->cap) ? pow2_at_least(tune->cap) : 2048;
+    if (cap < cap_min) cap = cap_min;
+    a.cap = cap;
+    size_t smem = qsmem_bytes(a.cap, a.kp, a.BR, a.B, NT);
+    while (smem + extra > 227 * 1024 && a.cap > cap_min) {
+        a.cap >>= 1;
+        smem = qsmem_bytes(a.cap, a.kp, a.BR, a.B, NT);
+    }
+    *smem_out = smem;
+}
+
+template <int NT>
+const void *plain_kernel(uint32_t rp)
+{
+    switch (rp) {
+    case 1: return (const void *)k_query<NT, 1>;
+    case 2: return (const void *)k_query<NT, 2>;
+    case 4: return (const void *)k_query<NT, 4>;
+    default: return (const void *)k_query<NT, 8>;
+    }
+}
+
+template <int NT>
+const void *fused_kernel(uint32_t rp, bool srp)
+{
+    switch ((srp ? 10 : 0) + rp) {
+    case 1: return (const void *)k_query_fused<NT, 1, 1>;
+    case 2: return (const void *)k_query_fused<NT, 2, 1>;
+    case 4: return (const void *)k_query_fused<NT, 4, 1>;
+    case 8: return (const void *)k_query_fused<NT, 8, 1>;
+    case 11: return (const void *)k_query_fused<NT, 1, 2>;
+    case 12: return (const void *)k_query_fused<NT, 2, 2>;
+    case 14: return (const void *)k_query_fused<NT, 4, 2>;
+    default: return (const void *)k_query_fused<NT, 8, 2>;
+    }
 }
 
 }  // namespace
@@ -459,29 +722,172 @@ int query_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
                  const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
                  uint8_t *out_scores)
 {
+    constexpr int NT = 256;
     if (nq == 0) return FLINNG_OK;
     QArgs a = make_args(ix, qbuckets, nq);
     a.k = k;
     a.k_max = k_max;
-    a.kp = pow2_at_least(k_max > 1 ? k_max : 2);
-    // room for one full round of members after a compaction to k keys
-    a.cap = pow2_at_least(a.kp + 2 * kQT > 2048 ? a.kp + 2 * kQT : 2048);
     a.out_ids = out_ids;
     a.out_scores = out_scores;
-    size_t smem = qsmem_bytes(a.cap, a.kp, a.BR, a.B);
-    while (smem > 227 * 1024 && a.cap > a.kp + kQT) {       // large B*R: trade buffer for room
-        a.cap >>= 1;
-        smem = qsmem_bytes(a.cap, a.kp, a.BR, a.B);
-    }
-    if (smem > 227 * 1024 || a.cap < a.kp + kQT)
+    size_t smem;
+    pick_buffer(a, NT, nullptr, 0, &smem);
+    if (smem > 227 * 1024)
         return set_error(FLINNG_ERR_INVALID_ARG,
                          "query: k_max=%u with B*R=%u needs %zu bytes of shared memory (> 227 KB)",
                          k_max, a.BR, smem);
-    switch (ix->rp) {
-    case 1: return launch_query_rp<1>(a, smem, ix->stream);
-    case 2: return launch_query_rp<2>(a, smem, ix->stream);
-    case 4: return launch_query_rp<4>(a, smem, ix->stream);
-    default: return launch_query_rp<8>(a, smem, ix->stream);
+    const void *fn = plain_kernel<NT>(ix->rp);
+    if (smem > 48 * 1024)
+        FL_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    void *args[] = {&a};
+    FL_CUDA(cudaLaunchKernel(fn, dim3(nq), dim3(NT), args, smem, ix->stream));   // one CTA per query
+    count_launch();
+    return FLINNG_OK;
+}
+
+// Everything one fused launch needs: kernel, shape, shared memory and the
+// argument blocks (kept in this struct so that a graph node can point at them).
+struct FusedPlan {
+    QArgs a;
+    HArgs h;
+    const void *fn;
+    int threads;
+    size_t smem;
+    uint32_t grid;
+    void *args[2];
+};
+
+static int fused_prepare(flinng_index *ix, const FusedQuery &fq, const uint32_t *k, uint32_t k_max,
+                         uint32_t *out_ids, uint8_t *out_scores, const QueryTuning *tune,
+                         uint32_t grid_for, FusedPlan *P)
+{
+    const uint32_t nq = fq.nq;
+    const int NT = (tune && tune->threads == 128) ? 128 : 256;
+    QArgs &a = P->a;
+    HArgs &h = P->h;
+    a = make_args(ix, nullptr, nq);
+    a.k = k;
+    a.k_max = k_max;
+    a.out_ids = out_ids;
+    a.out_scores = out_scores;
+    h = HArgs{};
+    const bool srp = ix->cfg.metric == FLINNG_COSINE_SRP;
+    h.K = ix->cfg.K;
+    size_t hash_bytes = size_t((ix->cfg.L + 3) & ~3u) * 4;
+    if (srp) {
+        h.x = fq.x;
+        h.ldx = fq.ldx;
+        h.w = ix->srp_w;
+        h.d = ix->cfg.dim;
+        h.gamma2 = ix->srp_margin_gamma;
+        h.tiny = float(h.d) * ldexpf(1.0f, -146);
+        h.gamma64 = ix->srp_gamma64;
+        h.stats = ix->stats;
+        hash_bytes += size_t(h.d) * 4;
+    } else {
+        h.q_off = fq.off;
+        h.q_el = fq.elems;
+        h.nb = ix->P;
+        h.da = ix->doph_a;
+        h.db = ix->doph_b;
+        h.seed = ix->doph_seed;
+        h.ba = ix->bucket_a;
+        h.bc = ix->bucket_c;
+        hash_bytes += size_t(h.nb + (h.nb + 31) / 32) * 4;
+    }
+    hash_bytes = (hash_bytes + 15) & ~size_t(15);
+    size_t qbytes;
+    pick_buffer(a, NT, tune, hash_bytes, &qbytes);
+    h.hash_off = qbytes;
+    P->smem = qbytes + hash_bytes;
+    if (P->smem > 227 * 1024)
+        return set_error(FLINNG_ERR_INVALID_ARG, "fused query: %zu bytes of shared memory needed (> 227 KB)", P->smem);
+    P->fn = NT == 128 ? fused_kernel<128>(ix->rp, srp) : fused_kernel<256>(ix->rp, srp);
+    P->threads = NT;
+    if (P->smem > 48 * 1024)
+        FL_CUDA(cudaFuncSetAttribute(P->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem));
+    int per_sm = 0;
+    FL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P->fn, NT, P->smem));
+    if (per_sm < 1) per_sm = 1;
+    int sms = 0;
+    FL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device));
+    uint32_t want = (tune && tune->ctas_per_sm) ? tune->ctas_per_sm : uint32_t(per_sm);
+    if (want > uint32_t(per_sm)) want = per_sm;
+    uint64_t grid = uint64_t(sms) * want;
+    if (grid > grid_for) grid = grid_for;
+    P->grid = uint32_t(grid ? grid : 1);
+    P->args[0] = &P->a;
+    P->args[1] = &P->h;
+    return FLINNG_OK;
+}
+
+int query_fused_launch(flinng_index *ix, const FusedQuery &fq, const uint32_t *k, uint32_t k_max,
+                       uint32_t *out_ids, uint8_t *out_scores, const QueryTuning *tune)
+{
+    if (fq.nq == 0) return FLINNG_OK;
+    FusedPlan P;
+    FL_TRY(fused_prepare(ix, fq, k, k_max, out_ids, out_scores, tune, fq.nq, &P));
+    if (ix->cfg.metric == FLINNG_COSINE_SRP)
+        FL_CUDA(cudaMemsetAsync(ix->stats, 0, 2 * sizeof(unsigned long long), ix->stream));
+    FL_CUDA(cudaLaunchKernel(P.fn, dim3(P.grid), dim3(P.threads), P.args, P.smem, ix->stream));
+    count_launch();
+    return FLINNG_OK;
+}
+
+// Graph form: one CUDA graph per batch-size class (nq rounded up to a power
+// of two) and per result width, built once and replayed; each call only
+// rewrites the kernel node's arguments (query and output pointers, nq).
+int query_graph_launch(flinng_index *ix, const FusedQuery &fq, const uint32_t *k, uint32_t k_max,
+                       uint32_t *out_ids, uint8_t *out_scores, const QueryTuning *tune)
+{
+    const uint32_t nq = fq.nq;
+    if (nq == 0) return FLINNG_OK;
+    uint32_t bucket = 0;
+    while ((1u << bucket) < nq) ++bucket;
+    FusedPlan P;
+    FL_TRY(fused_prepare(ix, fq, k, k_max, out_ids, out_scores, tune, 1u << bucket, &P));
+    QueryGraph &g = ix->graphs[bucket];
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void *>(P.fn);
+    kp.gridDim = dim3(P.grid);
+    kp.blockDim = dim3(P.threads);
+    kp.sharedMemBytes = (unsigned)P.smem;
+    kp.kernelParams = P.args;
+    const bool srp = ix->cfg.metric == FLINNG_COSINE_SRP;
+    if (!g.exec || g.fn != P.fn || g.smem != P.smem || g.grid != P.grid) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        g = QueryGraph{};
+        FL_CUDA(cudaGraphCreate(&g.graph, 0));
+        cudaGraphNode_t dep = nullptr;
+        if (srp) {
+            cudaMemsetParams mp{};
+            mp.dst = ix->stats;
+            mp.value = 0;
+            mp.elementSize = 4;
+            mp.width = 4;        // 2 x 64-bit counters
+            mp.height = 1;
+            mp.pitch = 0;
+            FL_CUDA(cudaGraphAddMemsetNode(&dep, g.graph, nullptr, 0, &mp));
+        }
+        FL_CUDA(cudaGraphAddKernelNode(&g.node, g.graph, dep ? &dep : nullptr, dep ? 1 : 0, &kp));
+        FL_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
+        g.fn = P.fn;
+        g.smem = P.smem;
+        g.grid = P.grid;
+    } else {
+        FL_CUDA(cudaGraphExecKernelNodeSetParams(g.exec, g.node, &kp));
+    }
+    FL_CUDA(cudaGraphLaunch(g.exec, ix->stream));
+    count_launch();
+    return FLINNG_OK;
+}
+
+void destroy_graphs(flinng_index *ix)
+{
+    for (QueryGraph &g : ix->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        g = QueryGraph{};
     }
 }
 
@@ -493,10 +899,10 @@ int counts_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
     a.cap = 2;
     a.kp = 2;
     a.out_counts = out_counts;
-    const size_t smem = qsmem_bytes(a.cap, a.kp, a.BR, a.B);
+    const size_t smem = qsmem_bytes(a.cap, a.kp, a.BR, a.B, kQTmax);
     if (smem > 48 * 1024)
         FL_CUDA(cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_counts<<<nq, kQT, smem, ix->stream>>>(a);
+    k_counts<<<nq, kQTmax, smem, ix->stream>>>(a);
     count_launch();
     FL_CUDA(cudaGetLastError());
     return FLINNG_OK;

@@ -20,6 +20,7 @@ from . import _build
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT = range(6)
 COSINE_SRP, JACCARD_DOPH = 0, 1
 PREC_FP32 = 0
+QUERY_PLAIN, QUERY_FUSED, QUERY_GRAPH = 0, 1, 2
 
 
 class flinng_config(C.Structure):
@@ -62,6 +63,9 @@ _SIGS = {
                                 C.POINTER(C.c_uint64), C.c_void_p]),
     "flinng_hash_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "flinng_kernel_launches": (C.c_uint64, []),
+    "flinng_set_query_mode": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "flinng_tune_query": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint32, C.c_uint32,
+                                    C.c_int, C.c_void_p]),
     "flinng_query_noalloc": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint32, C.c_void_p,
                                        C.c_uint32, C.c_void_p, C.c_void_p]),
 }
@@ -273,6 +277,16 @@ class Index:
         _check(self.lib.flinng_export(self.h, off.ctypes.data, cells.ctypes.data, cells.size,
                                       C.byref(nc), gid.ctypes.data))
         return {"off": off, "cells": cells[: nc.value], "gid": gid[: self.size]}
+
+    def set_query_mode(self, mode: int):
+        _check(self.lib.flinng_set_query_mode(self.h, mode))
+
+    def tune(self, q, k_max: int) -> dict:
+        """Autotune the fused query for batches of this size class."""
+        fp, nq, dev, keep = self._points(q)
+        ch = np.zeros(3, np.uint32)
+        _check(self.lib.flinng_tune_query(self.h, C.byref(fp), nq, k_max, dev, ch.ctypes.data))
+        return {"threads": int(ch[0]), "ctas_per_sm": int(ch[1]), "cap": int(ch[2])}
 
     def hash_stats(self):
         a, b = C.c_uint64(), C.c_uint64()

@@ -174,11 +174,16 @@ def test_counts_bit_exact(F):
         assert np.array_equal(got[i], O.counts(o.off, o.cells, L, K, qb[i], B * R))
 
 
+MODES = [0, 1, 2]     # flinng QUERY_PLAIN, QUERY_FUSED, QUERY_GRAPH
+
+
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("t_min", [1, 3])
-def test_query_dense_bit_exact(F, t_min):
+def test_query_dense_bit_exact(F, t_min, mode):
     N, d, R, B, L, K = 10_000, 128, 3, 100, 16, 12      # the paper-shaped cosine config
     pts, q, w, perm = dense_case(WL.config_seed(1), N, d, 100, R, B, L, K)
     ix = F.Index("cosine", R, B, L, K, capacity=N, params=w, dim=d, t_min=t_min)
+    ix.set_query_mode(mode)
     ix.build(pts, perm)
     o = oracle_index("cosine", R, B, L, K, K, w, pts, perm, t_min=t_min)
     ids, sc = ix.query(q, 10)
@@ -187,10 +192,14 @@ def test_query_dense_bit_exact(F, t_min):
     assert np.array_equal(sc, osc)
 
 
-def test_query_ragged_k_and_edge_cases(F):
+@pytest.mark.parametrize("mode", MODES)
+def test_query_ragged_k_and_edge_cases(F, mode):
     N, d, R, B, L, K = 1500, 32, 2, 40, 8, 6
     pts, q, w, perm = dense_case(8, N, d, 97, R, B, L, K)
+    q[5] = 0.0                    # zero query: every projection takes the exact path
+    q[9, :] = pts[3]              # exact copy of an indexed point
     ix = F.Index("cosine", R, B, L, K, capacity=N, params=w, dim=d)
+    ix.set_query_mode(mode)
     ix.build(pts, perm)
     o = oracle_index("cosine", R, B, L, K, K, w, pts, perm)
     rng = np.random.default_rng(8)
@@ -211,9 +220,11 @@ def test_query_ragged_k_and_edge_cases(F):
         ix.query(q, 10, k=np.full(q.shape[0], 11, np.uint32))
 
 
-def test_query_empty_index_and_empty_batch(F):
+@pytest.mark.parametrize("mode", MODES)
+def test_query_empty_index_and_empty_batch(F, mode):
     w = WL.srp_projections(9, 4 * 3, 8)
     ix = F.Index("cosine", 2, 5, 4, 3, capacity=10, params=w, dim=8)
+    ix.set_query_mode(mode)
     q = np.ones((3, 8), np.float32)
     ids, sc = ix.query(q, 4)
     assert np.all(u32(ids) == 0xFFFFFFFF) and np.all(sc == 0)
@@ -221,10 +232,19 @@ def test_query_empty_index_and_empty_batch(F):
     assert ids.shape == (0, 4)
 
 
-def test_query_sets_bit_exact(F):
+@pytest.mark.parametrize("mode", MODES)
+def test_query_sets_bit_exact(F, mode):
     N, nq, R, B, L, K, W = 4000, 200, 2, 1000, 32, 2, 17
     pts, q, dp, perm = sets_case(10, N, nq, R, L, K)
+    # ragged query sets: empty, single element, duplicates
+    qoff, qel = q
+    rows = [qel[qoff[i]:qoff[i + 1]] for i in range(nq)]
+    rows[0] = rows[0][:0]
+    rows[1] = rows[1][:1]
+    rows[2] = np.concatenate([rows[2], rows[2][:50]])
+    q = WL.csr_from_rows(rows)
     ix = F.Index("jaccard", R, B, L, K, capacity=N, params=dp, W=W)
+    ix.set_query_mode(mode)
     ix.build(pts, perm)
     o = oracle_index("jaccard", R, B, L, K, W, dp, pts, perm)
     ex = ix.export()
@@ -234,11 +254,13 @@ def test_query_sets_bit_exact(F):
     assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)
 
 
-def test_query_device_buffers_match_host(F):
+@pytest.mark.parametrize("mode", MODES)
+def test_query_device_buffers_match_host(F, mode):
     import torch
     N, nq, R, B, L, K, W = 3000, 100, 2, 300, 16, 2, 12
     pts, q, dp, perm = sets_case(11, N, nq, R, L, K)
     ix = F.Index("jaccard", R, B, L, K, capacity=N, params=dp, W=W)
+    ix.set_query_mode(mode)
     ix.build((torch.from_numpy(pts[0].view(np.int64)).cuda(), torch.from_numpy(pts[1].view(np.int32)).cuda()),
              torch.from_numpy(perm.view(np.int32)).cuda())
     torch.cuda.synchronize()
@@ -250,3 +272,83 @@ def test_query_device_buffers_match_host(F):
     o = oracle_index("jaccard", R, B, L, K, W, dp, pts, perm)
     oids, osc = o.query(q, 50)
     assert np.array_equal(u32(hid), oids)
+
+
+@pytest.mark.parametrize("R,B,L,K,W,k", [(4, 500, 64, 1, 17, 10), (3, 2000, 24, 2, 14, 1000), (1, 3000, 8, 3, 12, 7)])
+def test_fused_equals_plain_and_oracle_sets(F, R, B, L, K, W, k):
+    N, nq = 3000, 150
+    pts, q, dp, perm = sets_case(12 + R, N, nq, R, L, K)
+    ix = F.Index("jaccard", R, B, L, K, capacity=N, params=dp, W=W)
+    ix.build(pts, perm)
+    ix.set_query_mode(0)
+    pids, psc = ix.query(q, k)
+    ix.set_query_mode(1)
+    fids, fsc = ix.query(q, k)
+    assert np.array_equal(pids, fids) and np.array_equal(psc, fsc)
+    o = oracle_index("jaccard", R, B, L, K, W, dp, pts, perm)
+    oids, osc = o.query(q, k)
+    assert np.array_equal(u32(fids), oids) and np.array_equal(fsc, osc)
+
+
+@pytest.mark.parametrize("d,L,K", [(1, 4, 5), (67, 6, 9), (1024, 8, 16)])
+def test_fused_srp_equals_oracle(F, d, L, K):
+    N, R, B = 1200, 2, 60
+    pts, q, w, perm = dense_case(20 + d, N, d, 64, R, B, L, K, n_centers=10)
+    q[1] = 0.0
+    if d > 1:
+        for i in range(2, 64, 3):         # plant near-zero projections in the queries
+            j = i % (L * K)
+            q[i, -1] = np.float32(-float(np.dot(w[j, :-1].astype(np.float64), q[i, :-1])) / float(w[j, -1]))
+    ix = F.Index("cosine", R, B, L, K, capacity=N, params=w, dim=d)
+    ix.build(pts, perm)
+    ix.set_query_mode(1)
+    ids, sc = ix.query(q, 15)
+    o = oracle_index("cosine", R, B, L, K, K, w, pts, perm)
+    oids, osc = o.query(q, 15)
+    assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)
+    nre, nex = ix.hash_stats()
+    assert nex >= 1
+
+
+def test_graph_replay_and_tuning_keep_results(F):
+    # graph mode across calls of different sizes in the same and in different
+    # size classes, before and after autotuning, equals the plain form
+    N, nq, R, B, L, K, W = 3000, 300, 2, 300, 32, 2, 15
+    pts, q, dp, perm = sets_case(40, N, nq, R, L, K)
+    qoff, qel = q
+    ix = F.Index("jaccard", R, B, L, K, capacity=N, params=dp, W=W)
+    ix.build(pts, perm)
+
+    def sl(lo, hi):
+        return (qoff[lo:hi + 1] - qoff[lo]).astype(np.uint64), np.ascontiguousarray(qel[qoff[lo]:qoff[hi]])
+    ix.set_query_mode(0)
+    ref = {r: ix.query(sl(*r), 30) for r in [(0, 300), (10, 250), (5, 6), (0, 129)]}
+    ix.set_query_mode(2)
+    for r, (rid, rsc) in ref.items():
+        ids, sc = ix.query(sl(*r), 30)
+        assert np.array_equal(ids, rid) and np.array_equal(sc, rsc)
+    ch = ix.tune(sl(0, 300), 30)
+    assert ch["threads"] in (128, 256)
+    for r, (rid, rsc) in list(ref.items())[::-1]:
+        ids, sc = ix.query(sl(*r), 30)
+        assert np.array_equal(ids, rid) and np.array_equal(sc, rsc)
+    ix.set_query_mode(1)
+    ids, sc = ix.query(sl(0, 300), 30)
+    assert np.array_equal(ids, ref[(0, 300)][0])
+
+
+def test_graph_mode_cosine_stats_reset(F):
+    pts, q, w, perm = dense_case(41, 800, 40, 50, 2, 20, 6, 7)
+    q[0] = 0.0
+    ix = F.Index("cosine", 2, 20, 6, 7, capacity=800, params=w, dim=40)
+    ix.build(pts, perm)
+    ix.set_query_mode(2)
+    exact = []
+    for _ in range(3):
+        ids, sc = ix.query(q, 8)
+        exact.append(ix.hash_stats()[1])
+    # the zero query's 42 projections take the exact path; counters restart per call
+    assert exact[0] >= 6 * 7 and exact[0] == exact[1] == exact[2]
+    o = oracle_index("cosine", 2, 20, 6, 7, 7, w, pts, perm)
+    oids, osc = o.query(q, 8)
+    assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)
