@@ -329,6 +329,28 @@ void oracle_counts(const uint32_t *off, const uint16_t *cells, uint32_t L,
     }
 }
 
+/* Counts straight from the definition, with no reverse index (Sec. 5: a
+ * cell's count is the number of tables whose filter holds the query's
+ * bucket, i.e. in which some member of the cell shares it):
+ * cnt[r*B + gid[x][r]] counts table l once if some x has bucket[x][l] ==
+ * qbucket[l]. For sampled queries on indices too large to rebuild here. */
+void oracle_counts_direct(const uint32_t *bucket, const uint16_t *gid,
+                          uint64_t N, uint32_t L, uint32_t R, uint32_t B,
+                          const uint32_t *qbucket, uint8_t *cnt)
+{
+    const uint32_t BR = B * R;
+    uint8_t *hit = (uint8_t *)malloc(BR ? BR : 1);
+    for (uint32_t c = 0; c < BR; ++c) cnt[c] = 0;
+    for (uint32_t l = 0; l < L; ++l) {
+        memset(hit, 0, BR ? BR : 1);
+        for (uint64_t x = 0; x < N; ++x)
+            if (bucket[x * L + l] == qbucket[l])
+                for (uint32_t r = 0; r < R; ++r) hit[r * B + gid[x * R + r]] = 1;
+        for (uint32_t c = 0; c < BR; ++c) cnt[c] += hit[c];
+    }
+    free(hit);
+}
+
 /* ------------------------------------------------------------------------ */
 /* A7-A9: Alg. 3, threshold relaxation                                       */
 /* ------------------------------------------------------------------------ */

@@ -71,6 +71,9 @@ def lib():
                                    C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                    u32, C.c_uint64, C.c_void_p, C.c_uint32, u32, u8]
         L.oracle_query.restype = C.c_int
+        L.oracle_counts_direct.argtypes = [u32, u16, C.c_uint64, C.c_uint32, C.c_uint32,
+                                           C.c_uint32, u32, u8]
+        L.oracle_counts_direct.restype = None
         L.oracle_alg3.argtypes = [u8, u64, u32, C.c_uint64, C.c_uint32, C.c_uint32,
                                   C.c_uint32, C.c_uint32, u32, u8, C.c_uint32]
         L.oracle_alg3.restype = C.c_uint32
@@ -167,6 +170,17 @@ def counts(off, cells, L: int, W: int, qbucket, BR: int):
     cnt = np.zeros(BR, np.uint8)
     cells = _c(cells, np.uint16) if len(cells) else np.zeros(1, np.uint16)
     lib().oracle_counts(_c(off, np.uint32), cells, L, W, _c(qbucket, np.uint32), BR, cnt)
+    return cnt
+
+
+def counts_direct(buckets, gid, B: int, qbucket):
+    """Per-cell counts from the definition (no reverse index)."""
+    buckets = _c(buckets, np.uint32)
+    gid = _c(gid, np.uint16)
+    N, L = buckets.shape
+    R = gid.shape[1]
+    cnt = np.zeros(B * R, np.uint8)
+    lib().oracle_counts_direct(buckets, gid, N, L, R, B, _c(qbucket, np.uint32), cnt)
     return cnt
 
 

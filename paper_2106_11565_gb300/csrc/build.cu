@@ -92,6 +92,26 @@ __global__ void k_member_scatter(const uint16_t *__restrict__ gid, uint64_t N, u
     }
 }
 
+// Repetition-0 member records, in member-list order: word 0 = point id,
+// words 1.. = group ids of repetitions 1..R-1, two per word (low half first).
+__global__ void k_member_records(const uint32_t *__restrict__ mem, const uint16_t *__restrict__ gid,
+                                 uint64_t N, uint32_t R, uint32_t rp, uint32_t rw,
+                                 uint32_t *__restrict__ rec)
+{
+    for (uint64_t m = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; m < N;
+         m += uint64_t(gridDim.x) * blockDim.x) {
+        const uint32_t x = mem[m];
+        const uint16_t *g = gid + uint64_t(x) * rp;
+        rec[m * rw] = x;
+        for (uint32_t w = 1; w < rw; ++w) {
+            const uint32_t r = 2 * (w - 1) + 1;
+            const uint32_t lo = r < R ? g[r] : 0u;
+            const uint32_t hi = r + 1 < R ? g[r + 1] : 0u;
+            rec[m * rw + w] = lo | (hi << 16);
+        }
+    }
+}
+
 __global__ void k_slot_hist(const uint32_t *__restrict__ buckets, uint64_t n, uint32_t L,
                             uint32_t W, uint32_t R, uint32_t *__restrict__ hist)
 {
@@ -231,7 +251,79 @@ __global__ void k_slot_compact(const uint32_t *__restrict__ toff, const uint32_t
     }
 }
 
+__global__ void k_heavy_flag(const uint32_t *__restrict__ off, uint64_t nslot, uint32_t heavy_min,
+                             uint32_t *__restrict__ flag)
+{
+    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nslot;
+         s += uint64_t(gridDim.x) * blockDim.x)
+        flag[s] = (off[s + 1] - off[s]) >= heavy_min ? 1u : 0u;
+}
+
+// hidx[s] = bitmap index of heavy slot s (exclusive prefix of the flags) or
+// kEmpty32; each heavy slot's bitmap is written by one warp.
+__global__ void k_heavy_fill(const uint32_t *__restrict__ off, const uint16_t *__restrict__ cells,
+                             const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pre,
+                             uint64_t nslot, uint32_t BRw, uint32_t *__restrict__ hidx,
+                             uint32_t *__restrict__ hbm)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t gw = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t s = gw; s < nslot; s += nw) {
+        const bool heavy = flag[s] != 0u;
+        if (lane == 0) hidx[s] = heavy ? pre[s] : kEmpty32;
+        if (!heavy) continue;
+        uint32_t *bm = hbm + uint64_t(pre[s]) * BRw;
+        for (uint32_t w = lane; w < BRw; w += 32) bm[w] = 0u;
+        __syncwarp();
+        const uint32_t beg = off[s], end = off[s + 1];
+        for (uint32_t t = beg + lane; t < end; t += 32) {
+            const uint32_t c = cells[t];
+            atomicOr(&bm[c >> 5], 1u << (c & 31));
+        }
+        __syncwarp();
+    }
+}
+
 }  // namespace
+
+// Cell bitmaps of the heavy slots (those whose list has >= heavy_min cells).
+// Uses the build scratch slot_a / slot_b; grows the bitmap array if needed.
+int build_heavy(flinng_index *ix, void *scan_ws)
+{
+    const cudaStream_t st = ix->stream;
+    const uint64_t nslot = ix->nslot;
+    k_heavy_flag<<<thread_blocks(nslot), 256, 0, st>>>(ix->off, nslot, ix->heavy_min, ix->slot_a);
+    count_launch();
+    FL_CUDA(cudaGetLastError());
+    FL_TRY(scan_exclusive(ix->slot_a, ix->slot_b, nslot, scan_ws, st));
+    FL_CUDA(cudaMemcpyAsync(ix->h_flag, ix->slot_b + nslot, 4, cudaMemcpyDeviceToHost, st));
+    FL_CUDA(cudaStreamSynchronize(st));
+    const uint32_t nh = *ix->h_flag;
+    if (ix->BRw * 32 < ix->BR || ix->BRw == 0)
+        return set_error(FLINNG_ERR_INVALID_ARG, "internal: cell bitmap width %u for B*R=%u", ix->BRw, ix->BR);
+    const uint64_t words = uint64_t(nh) * ix->BRw;
+    if (words > ix->hbm_words) {
+        if (ix->hbm) {
+            cudaFree(ix->hbm);
+            ix->device_bytes -= ix->hbm_words * 4;
+            ix->hbm = nullptr;
+            ix->hbm_words = 0;
+        }
+        const uint64_t want = words + words / 8 + ix->BRw;
+        FL_CUDA(cudaMalloc(&ix->hbm, want * 4));
+        ix->hbm_words = want;
+        ix->device_bytes += want * 4;
+    }
+    if (nh > 0 && (!ix->hbm || ix->hbm_words < words))
+        return set_error(FLINNG_ERR_OOM, "internal: no storage for %u cell bitmaps", nh);
+    k_heavy_fill<<<warp_blocks(nslot), kWarpsPerBlock * 32, 0, st>>>(ix->off, ix->cells, ix->slot_a, ix->slot_b,
+                                                                    nslot, ix->BRw, ix->hidx, ix->hbm);
+    count_launch();
+    FL_CUDA(cudaGetLastError());
+    ix->n_heavy = nh;
+    return FLINNG_OK;
+}
 
 size_t perm_check_workspace_bytes(uint32_t R, uint64_t n)
 {
@@ -295,6 +387,9 @@ int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *per
         k_member_scatter<<<thread_blocks(N * R), 256, 0, st>>>(ix->gid, N, R, B, rp, mcur, ix->mem);
         count_launch();
         FL_CUDA(cudaGetLastError());
+        k_member_records<<<thread_blocks(N), 256, 0, st>>>(ix->mem, ix->gid, N, R, rp, ix->rw, ix->mrec);
+        count_launch();
+        FL_CUDA(cudaGetLastError());
     }
 
     // reverse index: histogram of old lists + new entries per slot
@@ -339,6 +434,7 @@ int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *per
     FL_CUDA(cudaStreamSynchronize(st));
     ix->n_cells = *ix->h_flag;
     ix->n_points = N;
+    FL_TRY(build_heavy(ix, scan_ws));
     return FLINNG_OK;
 }
 

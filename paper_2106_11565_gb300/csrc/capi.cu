@@ -65,7 +65,8 @@ void free_index(flinng_index *ix)
 {
     if (!ix) return;
     destroy_graphs(ix);
-    void *ptrs[] = {ix->srp_w, ix->bucket_a, ix->bucket_c, ix->gid, ix->moff, ix->mem, ix->off,
+    void *ptrs[] = {ix->srp_w, ix->bucket_a, ix->bucket_c, ix->gid, ix->moff, ix->mem, ix->mrec, ix->off,
+                    ix->hidx, ix->hbm,
                     ix->cells, ix->cells_tmp, ix->slot_a, ix->slot_b, ix->cell_cnt, ix->flag,
                     ix->stats, ix->ws.ptr};
     for (void *p : ptrs)
@@ -251,7 +252,11 @@ int flinng_create(const flinng_config *cfg, const flinng_params *params, void *s
     const uint32_t L = cfg->L, K = cfg->K, R = cfg->R;
     ix->P = L * K;
     ix->rp = R == 1 ? 1 : R == 2 ? 2 : R <= 4 ? 4 : 8;
+    ix->rw = R == 1 ? 1 : R <= 3 ? 2 : R <= 7 ? 4 : 8;
     ix->BR = cfg->B * R;
+    ix->BRw = (ix->BR + 31) / 32;
+    // a heavy slot's bitmap (B*R bits) is no larger than its list (2 bytes a cell)
+    ix->heavy_min = ix->BR / 16 > 32 ? ix->BR / 16 : 32;
     ix->nslot = uint64_t(L) << cfg->range_bits;
     ix->entries_cap = uint64_t(L) * R * cfg->capacity;
     ix->query_mode = FLINNG_QUERY_FUSED;
@@ -267,7 +272,9 @@ int flinng_create(const flinng_config *cfg, const flinng_params *params, void *s
     ALLOC(gid, size_t(cfg->capacity) * ix->rp);
     ALLOC(moff, size_t(ix->BR) + 1);
     ALLOC(mem, size_t(R) * cfg->capacity);
+    ALLOC(mrec, size_t(ix->rw) * cfg->capacity);
     ALLOC(off, ix->nslot + 1);
+    ALLOC(hidx, ix->nslot + 1);
     ALLOC(cells, ix->entries_cap);
     ALLOC(cells_tmp, ix->entries_cap);
     ALLOC(slot_a, ix->nslot + 1);
@@ -303,6 +310,7 @@ int flinng_create(const flinng_config *cfg, const flinng_params *params, void *s
             ix->doph_seed = params->doph_seed;
         }
         chk(cudaMemsetAsync(ix->off, 0, (ix->nslot + 1) * sizeof(uint32_t), st), "zero off");
+        chk(cudaMemsetAsync(ix->hidx, 0xFF, (ix->nslot + 1) * sizeof(uint32_t), st), "clear hidx");
         chk(cudaMemsetAsync(ix->moff, 0, (size_t(ix->BR) + 1) * sizeof(uint32_t), st), "zero moff");
         chk(cudaMemsetAsync(ix->stats, 0, 2 * sizeof(unsigned long long), st), "zero stats");
         chk(cudaStreamSynchronize(st), "create sync");

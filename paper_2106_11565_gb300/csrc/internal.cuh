@@ -88,6 +88,7 @@ struct flinng_index {
     // shape
     uint32_t P;            // L * K projections / MinHash values per point
     uint32_t rp;           // gid row stride (R rounded up to 1, 2, 4 or 8)
+    uint32_t rw;           // words per repetition-0 member record (1, 2, 4 or 8)
     uint32_t BR;
     uint64_t nslot;        // L << W
     uint64_t entries_cap;  // L * R * capacity
@@ -98,7 +99,14 @@ struct flinng_index {
     uint16_t *gid;         // capacity x rp
     uint32_t *moff;        // BR + 1: members of cell c are mem[moff[c] .. moff[c+1])
     uint32_t *mem;         // R * capacity point ids
+    uint32_t *mrec;        // capacity * rw: repetition-0 members with their other group ids
     uint32_t *off;         // nslot + 1
+    uint32_t *hidx;        // nslot: index of the slot's cell bitmap, or kEmpty32 (light slot)
+    uint32_t *hbm;         // n_heavy x BRw words: bitmaps of the heavy slots' cell lists
+    uint64_t hbm_words;    // allocated words of hbm
+    uint32_t n_heavy;
+    uint32_t heavy_min;    // a slot with at least this many cells also gets a bitmap
+    uint32_t BRw;          // 32-bit words per cell bitmap
     uint16_t *cells;       // entries_cap
     uint16_t *cells_tmp;   // entries_cap (build scratch)
     uint32_t *slot_a;      // nslot + 1 (build scratch)
@@ -144,6 +152,7 @@ int check_perm(flinng_index *ix, const uint32_t *perm, uint64_t n, void *ws);
 size_t insert_workspace_bytes(const flinng_index *ix);
 int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *perm,
                   uint64_t n, void *ws);
+int build_heavy(flinng_index *ix, void *scan_ws);
 
 // ---- query.cu
 struct FusedQuery {

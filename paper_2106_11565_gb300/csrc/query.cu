@@ -40,10 +40,11 @@ struct QArgs {
     uint32_t k_max;
     const uint32_t *off;
     const uint16_t *cells;
-    const uint16_t *gid;
     const uint32_t *moff;
-    const uint32_t *mem;
-    uint32_t L, W, R, B, BR, t_min;
+    const uint32_t *mrec;     // repetition-0 member records (RW words each)
+    const uint32_t *hidx;     // per slot: heavy bitmap index or kEmpty32
+    const uint32_t *hbm;      // heavy slots' cell bitmaps, BRw words each
+    uint32_t L, W, R, B, BR, BRw, t_min;
     uint32_t cap;      // candidate buffer entries (power of two)
     uint32_t kp;       // final sort width: power of two >= k_max
     uint32_t *out_ids;
@@ -54,13 +55,17 @@ struct QArgs {
 struct QSmem {
     uint64_t *buf;       // cap candidate keys
     uint64_t *keep;      // kp keys (selection output, final sort)
-    uint32_t *u;         // 8 scalars: nbuf, nkeep, sel digit, sel rem, ...
+    uint32_t *u;         // 8 scalars: nbuf, nkeep, digit, rank, whole, heavy tables, bound (u[6..7])
     uint32_t *hist_s;    // 256: points seen, by score
     uint32_t *lvl_n;     // 256: repetition-0 cells per count
     uint32_t *lvl_cur;   // 256
     uint32_t *rhist;     // 256: radix histogram
     uint32_t *c_start;   // NT: member start of each cell of a chunk / list start
     uint32_t *c_pre;     // NT + 1: exclusive prefix of member counts
+    uint32_t *c_cell;    // NT: repetition-0 group of each cell of a chunk
+    uint32_t *g_beg;     // 256: list start per table (gather)
+    uint32_t *g_len;     // 256: list length per table, 0 for heavy tables
+    uint32_t *g_hl;      // 256: bitmap indices of the heavy tables
     uint32_t *wsum;      // NT / 32: block-scan scratch
     uint32_t *cntw;      // (BR + 3) / 4 words of byte counts
     uint16_t *lvl_cells; // B
@@ -68,7 +73,8 @@ struct QSmem {
 
 __host__ __device__ inline size_t qsmem_bytes(uint32_t cap, uint32_t kp, uint32_t BR, uint32_t B, int NT)
 {
-    size_t b = size_t(cap) * 8 + size_t(kp) * 8 + 8 * 4 + 4 * 256 * 4 + NT * 4 + (NT + 1) * 4 + (NT / 32) * 4;
+    size_t b = size_t(cap) * 8 + size_t(kp) * 8 + 8 * 4 + 4 * 256 * 4 + NT * 4 + (NT + 1) * 4 + NT * 4 +
+               3 * 256 * 4 + (NT / 32) * 4;
     b = (b + 15) & ~size_t(15);
     b += size_t((BR + 3) / 4) * 4;
     b += size_t(B) * 2;
@@ -88,7 +94,11 @@ __device__ inline QSmem carve_q(unsigned char *sm, uint32_t cap, uint32_t kp)
     s.rhist = s.lvl_cur + 256;
     s.c_start = s.rhist + 256;
     s.c_pre = s.c_start + NT;
-    s.wsum = s.c_pre + NT + 1;
+    s.c_cell = s.c_pre + NT + 1;
+    s.g_beg = s.c_cell + NT;
+    s.g_len = s.g_beg + 256;
+    s.g_hl = s.g_len + 256;
+    s.wsum = s.g_hl + 256;
     size_t o = (size_t)((unsigned char *)(s.wsum + NT / 32) - sm);
     o = (o + 15) & ~size_t(15);
     s.cntw = (uint32_t *)(sm + o);
@@ -100,22 +110,24 @@ __device__ inline uint16_t *lvl_cells_ptr(const QSmem &s, uint32_t BR)
     return (uint16_t *)(s.cntw + (BR + 3) / 4);
 }
 
-template <int RP>
-__device__ inline void load_gid(const uint16_t *__restrict__ gid, uint32_t x, uint32_t g[RP])
+// Member record of repetition 0: word 0 = point id, words 1.. = the group
+// ids of repetitions 1..R-1, two 16-bit ids per word.
+template <int RW>
+__device__ inline void load_record(const uint32_t *__restrict__ rec, uint32_t m, uint32_t w[RW])
 {
-    if constexpr (RP == 1) {
-        g[0] = gid[x];
-    } else if constexpr (RP == 2) {
-        const uint32_t v = __ldg(reinterpret_cast<const uint32_t *>(gid) + x);
-        g[0] = v & 0xFFFFu;
-        g[1] = v >> 16;
-    } else if constexpr (RP == 4) {
-        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(gid) + x);
-        g[0] = v.x & 0xFFFFu; g[1] = v.x >> 16; g[2] = v.y & 0xFFFFu; g[3] = v.y >> 16;
+    if constexpr (RW == 1) {
+        w[0] = __ldg(rec + m);
+    } else if constexpr (RW == 2) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(rec) + m);
+        w[0] = v.x; w[1] = v.y;
+    } else if constexpr (RW == 4) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(rec) + m);
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
     } else {
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(gid) + x);
-        g[0] = v.x & 0xFFFFu; g[1] = v.x >> 16; g[2] = v.y & 0xFFFFu; g[3] = v.y >> 16;
-        g[4] = v.z & 0xFFFFu; g[5] = v.z >> 16; g[6] = v.w & 0xFFFFu; g[7] = v.w >> 16;
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(rec) + 2 * size_t(m));
+        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(rec) + 2 * size_t(m) + 1);
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+        w[4] = u.x; w[5] = u.y; w[6] = u.z; w[7] = u.w;
     }
 }
 
@@ -169,9 +181,19 @@ __device__ void block_select(const uint64_t *keys, uint32_t n, uint32_t kk, cons
     for (int shift = 48; shift >= 0; shift -= 8) {
         for (int i = tid; i < 256; i += NT) s.rhist[i] = 0u;
         __syncthreads();
-        for (uint32_t i = tid; i < n; i += NT) {
-            const uint64_t v = keys[i];
-            if ((v & mask) == prefix) atomicAdd(&s.rhist[(v >> shift) & 0xFF], 1u);
+        // keys share their leading digits: aggregate per warp before the
+        // shared-memory atomic (one per distinct digit per warp)
+        for (uint32_t ib = tid & ~31u; ib < n; ib += NT) {
+            const uint32_t i = ib + lane;
+            bool in = false;
+            uint32_t dg = 256;
+            if (i < n) {
+                const uint64_t v = keys[i];
+                in = (v & mask) == prefix;
+                dg = in ? uint32_t((v >> shift) & 0xFF) : 256u;
+            }
+            const uint32_t grp = __match_any_sync(0xffffffffu, dg);
+            if (in && lane == __ffs(grp) - 1) atomicAdd(&s.rhist[dg], __popc(grp));
         }
         __syncthreads();
         if (tid < 32) {
@@ -222,38 +244,100 @@ __device__ void block_select(const uint64_t *keys, uint32_t n, uint32_t kk, cons
 }
 
 // Keep the kk best of buf[0..nbuf) in buf[0..kk); returns the new admission
-// bound (keys above it can never enter the top kk).
+// bound: the largest kept key (later keys above it can never enter the top kk).
 template <int NT>
 __device__ uint64_t block_compact(const QSmem &s, uint32_t nbuf, uint32_t kk)
 {
+    const int lane = threadIdx.x & 31;
     uint64_t prefix, mask;
     block_select<NT>(s.buf, nbuf, kk, s, prefix, mask);
     if (threadIdx.x == 0) s.u[1] = 0u;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nbuf; i += NT) {
-        const uint64_t v = s.buf[i];
-        if ((v & mask) <= prefix) s.keep[atomicAdd(&s.u[1], 1u)] = v;
+    for (uint32_t ib = threadIdx.x & ~31u; ib < nbuf; ib += NT) {
+        const uint32_t i = ib + lane;
+        const uint64_t v = i < nbuf ? s.buf[i] : kKeyNone;
+        const bool take = i < nbuf && (v & mask) <= prefix;
+        const uint32_t wm = __ballot_sync(0xffffffffu, take);
+        if (wm) {
+            uint32_t base = 0;
+            if (lane == __ffs(wm) - 1) base = atomicAdd(&s.u[1], __popc(wm));
+            base = __shfl_sync(0xffffffffu, base, __ffs(wm) - 1);
+            if (take) s.keep[base + __popc(wm & ((1u << lane) - 1u))] = v;
+        }
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < kk; i += NT) s.buf[i] = s.keep[i];
-    if (threadIdx.x == 0) s.u[0] = kk;
+    uint64_t mx = 0;
+    for (uint32_t i = threadIdx.x; i < kk; i += NT) {
+        const uint64_t v = s.keep[i];
+        s.buf[i] = v;
+        mx = v > mx ? v : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t y = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    // u[6..7]: one 64-bit word (8-byte aligned: u follows the 64-bit keep array)
+    if (threadIdx.x == 0) {
+        s.u[0] = kk;
+        s.u[6] = 0u;
+        s.u[7] = 0u;
+    }
     __syncthreads();
-    return prefix | (~mask & kKeyBits);
+    if (lane == 0 && mx) {
+        atomicMax(reinterpret_cast<unsigned long long *>(&s.u[6]), (unsigned long long)mx);
+    }
+    __syncthreads();
+    const uint64_t bound = *reinterpret_cast<const unsigned long long *>(&s.u[6]);
+    __syncthreads();
+    return bound;
 }
 
+// Per-cell collision counts of one query (Sec. 5). Tables whose bucket is
+// heavy contribute their cell bitmap: each thread owns whole counter words
+// and adds 4 bits at a time (spread to the 4 bytes of the word) without
+// atomics. The other tables' lists are flattened over the CTA and counted
+// with shared-memory atomics. Contains __syncthreads.
 template <int NT>
 __device__ void gather_counts(const QArgs &a, const QSmem &s, const uint32_t *qb)
 {
     const int tid = threadIdx.x;
-    // one thread per table: its list's start and length
-    for (uint32_t l0 = 0; l0 < a.L; l0 += NT) {
-        const uint32_t l = l0 + tid;
+    if (tid == 0) s.u[5] = 0u;
+    __syncthreads();
+    for (uint32_t l = tid; l < a.L; l += NT) {
+        const uint64_t slot = (uint64_t(l) << a.W) | qb[l];
+        const uint32_t h = a.hidx[slot];
         uint32_t beg = 0, len = 0;
-        if (l < a.L) {
-            const uint64_t slot = (uint64_t(l) << a.W) | qb[l];
+        if (h != kEmpty32) {
+            s.g_hl[atomicAdd(&s.u[5], 1u)] = h;
+        } else {
             beg = a.off[slot];
             len = a.off[slot + 1] - beg;
         }
+        s.g_beg[l] = beg;
+        s.g_len[l] = len;
+    }
+    __syncthreads();
+    const uint32_t nh = s.u[5];
+    if (nh > 0) {
+        const uint32_t nwords = (a.BR + 3) / 4;
+        for (uint32_t w = tid; w < a.BRw; w += NT) {
+            uint32_t acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (uint32_t i = 0; i < nh; ++i) {
+                const uint32_t x = __ldg(a.hbm + size_t(s.g_hl[i]) * a.BRw + w);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[j] += ((x >> (4 * j)) & 0xFu) * 0x00204081u & 0x01010101u;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (w * 8 + j < nwords) s.cntw[w * 8 + j] += acc[j];
+        }
+        __syncthreads();
+    }
+    for (uint32_t l0 = 0; l0 < a.L; l0 += NT) {
+        const uint32_t l = l0 + tid;
+        const uint32_t beg = l < a.L ? s.g_beg[l] : 0u;
+        const uint32_t len = l < a.L ? s.g_len[l] : 0u;
         uint32_t total;
         const uint32_t pre = block_excl_scan<NT>(len, s.wsum, &total);
         s.c_start[tid] = beg;
@@ -284,12 +368,12 @@ __device__ inline void zero_query_state(const QArgs &a, const QSmem &s)
 
 // Group tests, AND-over-R decode and top-k of query q, from the counts in
 // shared memory; writes row q of the outputs.
-template <int NT, int RP>
+template <int NT, int RW>
 __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t kq)
 {
     uint16_t *lvl_cells = lvl_cells_ptr(s, a.BR);
     const uint8_t *cnt8 = reinterpret_cast<const uint8_t *>(s.cntw);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     if (kq > 0) {
         // group tests of repetition 0, bucketed by count level
         for (uint32_t b = tid; b < a.B; b += NT) {
@@ -319,9 +403,9 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
             const uint32_t first = s.lvl_cur[t] - nc;
             for (uint32_t c0 = 0; c0 < nc; c0 += NT) {
                 const uint32_t ci = c0 + tid;
-                uint32_t ms = 0, sz = 0;
+                uint32_t ms = 0, sz = 0, b = 0;
                 if (ci < nc) {
-                    const uint32_t b = lvl_cells[first + ci];
+                    b = lvl_cells[first + ci];
                     ms = a.moff[b];
                     sz = a.moff[b + 1] - ms;
                 }
@@ -329,34 +413,52 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                 const uint32_t pre = block_excl_scan<NT>(sz, s.wsum, &M);
                 s.c_start[tid] = ms;
                 s.c_pre[tid] = pre;
+                s.c_cell[tid] = b;
                 const uint32_t ncc = min(uint32_t(NT), nc - c0);
                 __syncthreads();
                 for (uint32_t j0 = 0; j0 < M; j0 += sub) {
                     const uint32_t jn = min(M, j0 + sub);
                     if (s.u[0] + (jn - j0) > a.cap) bound = block_compact<NT>(s, s.u[0], kq);
-                    for (uint32_t j = j0 + tid; j < jn; j += NT) {
-                        const uint32_t cs = find_seg(s.c_pre, ncc, j);
-                        const uint32_t x = __ldg(a.mem + s.c_start[cs] + (j - s.c_pre[cs]));
-                        uint32_t g[RP];
-                        load_gid<RP>(a.gid, x, g);
-                        uint32_t score = 256, last = 0;
+                    // warp-uniform trip count: every lane of a warp runs every iteration
+                    for (uint32_t jb = j0 + (tid & ~31u); jb < jn; jb += NT) {
+                        const uint32_t j = jb + lane;
+                        bool valid = false;
+                        uint32_t score = 256, last = 0, x = 0;
+                        if (j < jn) {
+                            const uint32_t cs = find_seg(s.c_pre, ncc, j);
+                            uint32_t w[RW];
+                            load_record<RW>(a.mrec, s.c_start[cs] + (j - s.c_pre[cs]), w);
+                            x = w[0];
+                            // repetition 0: the cell itself, at count t
+                            score = uint32_t(t);
+                            last = s.c_cell[cs];
 #pragma unroll
-                        for (int r = 0; r < RP; ++r) {
-                            if (r < int(a.R)) {
-                                const uint32_t c = uint32_t(r) * a.B + g[r];
-                                const uint32_t v = cnt8[c];
-                                if (v < score) {
-                                    score = v;
-                                    last = c;
-                                } else if (v == score) {
-                                    last = c;
+                            for (int r = 1; r < 2 * RW - 1; ++r) {
+                                if (r < int(a.R)) {
+                                    const uint32_t g = (w[1 + (r - 1) / 2] >> (16 * ((r - 1) & 1))) & 0xFFFFu;
+                                    const uint32_t c = uint32_t(r) * a.B + g;
+                                    const uint32_t v = cnt8[c];
+                                    if (v < score) {
+                                        score = v;
+                                        last = c;
+                                    } else if (v == score) {
+                                        last = c;
+                                    }
                                 }
                             }
+                            valid = score >= a.t_min;
                         }
-                        if (score >= a.t_min) {
-                            atomicAdd(&s.hist_s[score], 1u);
-                            const uint64_t key = (uint64_t(255u - score) << 48) | (uint64_t(last) << 32) | x;
-                            if (key <= bound) s.buf[atomicAdd(&s.u[0], 1u)] = key;
+                        // points seen per score: one shared-memory atomic per distinct score per warp
+                        const uint32_t grp = __match_any_sync(0xffffffffu, valid ? score : 0xFFFFu);
+                        if (valid && lane == __ffs(grp) - 1) atomicAdd(&s.hist_s[score], __popc(grp));
+                        const uint64_t key = (uint64_t(255u - score) << 48) | (uint64_t(last) << 32) | x;
+                        const bool want = valid && key <= bound;
+                        const uint32_t wm = __ballot_sync(0xffffffffu, want);
+                        if (wm) {
+                            uint32_t base = 0;
+                            if (lane == __ffs(wm) - 1) base = atomicAdd(&s.u[0], __popc(wm));
+                            base = __shfl_sync(0xffffffffu, base, __ffs(wm) - 1);
+                            if (want) s.buf[base + __popc(wm & ((1u << lane) - 1u))] = key;
                         }
                     }
                     __syncthreads();
@@ -399,7 +501,7 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
     __syncthreads();
 }
 
-template <int NT, int RP>
+template <int NT, int RW>
 __global__ void __launch_bounds__(NT, 2048 / NT)
 k_query(QArgs a)
 {
@@ -411,7 +513,7 @@ k_query(QArgs a)
         zero_query_state<NT>(a, s);
         __syncthreads();
         if (kq > 0) gather_counts<NT>(a, s, a.qb + size_t(q) * a.L);
-        decode_topk<NT, RP>(a, s, q, kq);
+        decode_topk<NT, RW>(a, s, q, kq);
     }
 }
 
@@ -606,7 +708,7 @@ __device__ void cta_srp(const QArgs &a, const HArgs &h, uint32_t q, uint32_t *qb
     __syncthreads();
 }
 
-template <int NT, int RP, int HASH>
+template <int NT, int RW, int HASH>
 __global__ void __launch_bounds__(NT, (HASH == 2 ? 1024 : 2048) / NT)
 k_query_fused(QArgs a, HArgs h)
 {
@@ -625,7 +727,7 @@ k_query_fused(QArgs a, HArgs h)
         } else {
             __syncthreads();
         }
-        decode_topk<NT, RP>(a, s, q, kq);
+        decode_topk<NT, RW>(a, s, q, kq);
     }
 }
 
@@ -661,9 +763,11 @@ QArgs make_args(flinng_index *ix, const uint32_t *qb, uint32_t nq)
     a.nq = nq;
     a.off = ix->off;
     a.cells = ix->cells;
-    a.gid = ix->gid;
     a.moff = ix->moff;
-    a.mem = ix->mem;
+    a.mrec = ix->mrec;
+    a.hidx = ix->hidx;
+    a.hbm = ix->hbm;
+    a.BRw = ix->BRw;
     a.L = ix->cfg.L;
     a.W = ix->cfg.range_bits;
     a.R = ix->cfg.R;
@@ -691,9 +795,9 @@ void pick_buffer(QArgs &a, int NT, const QueryTuning *tune, size_t extra, size_t
 }
 
 template <int NT>
-const void *plain_kernel(uint32_t rp)
+const void *plain_kernel(uint32_t rw)
 {
-    switch (rp) {
+    switch (rw) {
     case 1: return (const void *)k_query<NT, 1>;
     case 2: return (const void *)k_query<NT, 2>;
     case 4: return (const void *)k_query<NT, 4>;
@@ -702,9 +806,9 @@ const void *plain_kernel(uint32_t rp)
 }
 
 template <int NT>
-const void *fused_kernel(uint32_t rp, bool srp)
+const void *fused_kernel(uint32_t rw, bool srp)
 {
-    switch ((srp ? 10 : 0) + rp) {
+    switch ((srp ? 10 : 0) + rw) {
     case 1: return (const void *)k_query_fused<NT, 1, 1>;
     case 2: return (const void *)k_query_fused<NT, 2, 1>;
     case 4: return (const void *)k_query_fused<NT, 4, 1>;
@@ -735,7 +839,7 @@ int query_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
         return set_error(FLINNG_ERR_INVALID_ARG,
                          "query: k_max=%u with B*R=%u needs %zu bytes of shared memory (> 227 KB)",
                          k_max, a.BR, smem);
-    const void *fn = plain_kernel<NT>(ix->rp);
+    const void *fn = plain_kernel<NT>(ix->rw);
     if (smem > 48 * 1024)
         FL_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     void *args[] = {&a};
@@ -801,7 +905,7 @@ static int fused_prepare(flinng_index *ix, const FusedQuery &fq, const uint32_t 
     P->smem = qbytes + hash_bytes;
     if (P->smem > 227 * 1024)
         return set_error(FLINNG_ERR_INVALID_ARG, "fused query: %zu bytes of shared memory needed (> 227 KB)", P->smem);
-    P->fn = NT == 128 ? fused_kernel<128>(ix->rp, srp) : fused_kernel<256>(ix->rp, srp);
+    P->fn = NT == 128 ? fused_kernel<128>(ix->rw, srp) : fused_kernel<256>(ix->rw, srp);
     P->threads = NT;
     if (P->smem > 48 * 1024)
         FL_CUDA(cudaFuncSetAttribute(P->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem));

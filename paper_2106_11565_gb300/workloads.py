@@ -172,49 +172,71 @@ def genomic_reads(seed: int, ref_len: int, n_reads: int, read_len: int,
 _ALPHABET = np.frombuffer(b"abcdefghijklmnopqrstuvwxyz0123456789", dtype=np.uint8)
 
 
-def _gram_sets(strings: list[bytes]) -> list[np.ndarray]:
-    rows = []
-    for s in strings:
-        b = np.frombuffer(s, dtype=np.uint8).astype(U32)
-        if len(b) < 3:
-            rows.append(np.zeros(0, U32))
-            continue
-        g = (b[:-2] << U32(16)) | (b[1:-1] << U32(8)) | b[2:]
-        rows.append(np.unique(g).astype(U32))
-    return rows
+def _gram_csr(buf: np.ndarray, off: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Sets of character 3-grams of the strings buf[off[i]:off[i+1]]; a gram
+    is its 3 bytes packed into 24 bits (exact); each set sorted, deduplicated."""
+    n = off.size - 1
+    lens = np.diff(off)
+    total = int(off[-1])
+    if total < 3:
+        return np.zeros(n + 1, U64), np.zeros(0, U32)
+    b = buf[:total].astype(np.uint32)
+    g = (b[:-2] << np.uint32(16)) | (b[1:-1] << np.uint32(8)) | b[2:]
+    owner = np.repeat(np.arange(n, dtype=np.int64), lens)[:-2]
+    pos = np.arange(total - 2, dtype=np.int64)
+    ok = pos + 2 < off[owner + 1]
+    key = (owner[ok].astype(U64) << U64(24)) | g[ok].astype(U64)
+    key.sort()
+    keep = np.ones(key.size, bool)
+    keep[1:] = key[1:] != key[:-1]
+    key = key[keep]
+    sid = (key >> U64(24)).astype(np.int64)
+    cnt = np.bincount(sid, minlength=n)
+    csr = np.zeros(n + 1, U64)
+    csr[1:] = np.cumsum(cnt)
+    return csr, (key & U64(0xFFFFFF)).astype(U32)
 
 
 def url_strings(seed: int, n: int, n_queries: int, vocab: int = 50_000,
-                zipf_s: float = 1.1, median_len: float = 60.0,
-                sigma: float = 0.5, edit_rate: float = 0.05) -> dict:
+                zipf_s: float = 1.1, median_len: float = 60.0, sigma: float = 0.5,
+                edit_rate: float = 0.05) -> dict:
     """URL-shaped strings turned into sets of character 3-grams.
 
-    Tokens are random [a-z0-9] words of length 2..12 drawn from a vocabulary
-    by a Zipf(zipf_s) law; a string is tokens joined by '/' until its
-    lognormal target length (median ``median_len``) is reached. A 3-gram is
-    its 3 bytes packed into 24 bits (exact). Queries are copies of random
-    strings with ``edit_rate`` character edits (substitution, insertion or
-    deletion with equal probability).
+    A vocabulary of ``vocab`` random [a-z0-9] tokens of length 2..12 is drawn;
+    a long stream of tokens is sampled by a Zipf(``zipf_s``) law over the
+    vocabulary ranks and joined with '/'. String i is the next slice of the
+    stream whose length is drawn lognormal (median ``median_len``, log-sd
+    ``sigma``, at least 3). Queries are copies of random strings with
+    ``edit_rate`` x length character edits (substitution, insertion or
+    deletion with equal probability, at least one).
     """
     rng = np.random.default_rng([seed, 40])
-    tok_len = rng.integers(2, 13, size=vocab)
-    tok = [bytes(_ALPHABET[rng.integers(0, len(_ALPHABET), size=int(t))]) for t in tok_len]
-    w = 1.0 / np.arange(1, vocab + 1) ** zipf_s
-    cdf = np.cumsum(w / w.sum())
-    target = np.maximum(3, np.round(rng.lognormal(np.log(median_len), sigma, size=n))).astype(int)
-    strings = []
-    for i in range(n):
-        parts = []
-        ln = 0
-        while ln < target[i]:
-            t = tok[int(np.searchsorted(cdf, rng.random()))]
-            parts.append(t)
-            ln += len(t) + 1
-        strings.append(b"/".join(parts)[: int(target[i])])
+    tok_len = rng.integers(2, 13, size=vocab).astype(np.int64)
+    tok_chars = _ALPHABET[rng.integers(0, len(_ALPHABET), size=(vocab, 12))]
+    w = 1.0 / np.arange(1, vocab + 1, dtype=np.float64) ** zipf_s
+    w /= w.sum()
+    cdf = np.cumsum(w)
+    target = np.maximum(3, np.round(rng.lognormal(np.log(median_len), sigma, size=n))).astype(np.int64)
+    total = int(target.sum())
+    mean_tok = float((tok_len + 1) @ w)
+    n_tok = int(total / mean_tok * 1.1) + 1024
+    while True:
+        toks = np.minimum(np.searchsorted(cdf, rng.random(n_tok)), vocab - 1)
+        tl = tok_len[toks]
+        if int((tl + 1).sum()) >= total:
+            break
+        n_tok = int(n_tok * 1.2)
+    starts = np.cumsum(tl + 1) - (tl + 1)
+    stream = np.full(int((tl + 1).sum()), ord("/"), np.uint8)
+    within = np.arange(int(tl.sum()), dtype=np.int64) - np.repeat(np.cumsum(tl) - tl, tl)
+    stream[np.repeat(starts, tl) + within] = tok_chars[np.repeat(toks, tl), within]
+    del within
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum(target)
     src = rng.integers(0, n, size=n_queries)
-    queries = []
+    qrows = []
     for i in src:
-        s = bytearray(strings[int(i)])
+        s = bytearray(stream[off[i]:off[i + 1]].tobytes())
         n_ed = max(1, int(round(edit_rate * len(s))))
         for _ in range(n_ed):
             op = int(rng.integers(0, 3))
@@ -226,7 +248,11 @@ def url_strings(seed: int, n: int, n_queries: int, vocab: int = 50_000,
                 s.insert(pos, ch)
             elif len(s) > 1:
                 del s[pos]
-        queries.append(bytes(s))
-    off, el = csr_from_rows(_gram_sets(strings))
-    qoff, qel = csr_from_rows(_gram_sets(queries))
-    return {"off": off, "elems": el, "q_off": qoff, "q_elems": qel, "src": src}
+        qrows.append(np.frombuffer(bytes(s), np.uint8))
+    qoff = np.zeros(n_queries + 1, np.int64)
+    qoff[1:] = np.cumsum([len(r) for r in qrows])
+    qbuf = np.concatenate(qrows) if qrows else np.zeros(0, np.uint8)
+    soff, sel = _gram_csr(stream, off)
+    qsoff, qsel = _gram_csr(qbuf, qoff)
+    return {"off": soff, "elems": sel, "q_off": qsoff, "q_elems": qsel, "src": src,
+            "str_len": target}

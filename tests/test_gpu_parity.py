@@ -352,3 +352,32 @@ def test_graph_mode_cosine_stats_reset(F):
     o = oracle_index("cosine", 2, 20, 6, 7, 7, w, pts, perm)
     oids, osc = o.query(q, 8)
     assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_heavy_bucket_bitmaps(F, mode):
+    # 2-bit buckets: every list is long, most slots get a cell bitmap; a few
+    # 9-bit tables stay light: counts and top-k must not change
+    N, d, R, B = 2500, 24, 3, 60
+    pts, q, w, perm = dense_case(50, N, d, 80, R, B, 6, 2)
+    ix = F.Index("cosine", R, B, 6, 2, capacity=N, params=w, dim=d)
+    ix.set_query_mode(mode)
+    ix.build(pts, perm)
+    o = oracle_index("cosine", R, B, 6, 2, 2, w, pts, perm)
+    qb = O.srp_codes(q, w, 6, 2)
+    got = ix.counts(qb)
+    for i in range(q.shape[0]):
+        assert np.array_equal(got[i], O.counts(o.off, o.cells, 6, 2, qb[i], B * R))
+    ids, sc = ix.query(q, 40)
+    oids, osc = o.query(q, 40)
+    assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)
+    # mixed heavy and light tables in one query
+    pts2, q2, w2, perm2 = dense_case(51, N, d, 80, R, B, 10, 9)
+    w2[:18] = w2[:18] * 0 + w[:1]          # tables 0-1 use one projection repeatedly: 2 buckets
+    jx = F.Index("cosine", R, B, 10, 9, capacity=N, params=w2, dim=d)
+    jx.set_query_mode(mode)
+    jx.build(pts2, perm2)
+    o2 = oracle_index("cosine", R, B, 10, 9, 9, w2, pts2, perm2)
+    ids, sc = jx.query(q2, 25)
+    oids, osc = o2.query(q2, 25)
+    assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)

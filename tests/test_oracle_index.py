@@ -239,3 +239,14 @@ def test_insert_equals_build_of_union():
             assert a.gid[200 + p2[r, i], r] == (200 + i) % 7
     b_off, b_cells = O.build_csr(a.buckets, a.gid, 7, 5)
     assert np.array_equal(a.off, b_off) and np.array_equal(a.cells, b_cells)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_counts_direct_equals_index_walk(seed):
+    N, L, R, B, W = 300, 7, 3, 13, 4
+    buckets, gid = _tiny_index(seed, N, L, R, B, W)
+    off, cells = O.build_csr(buckets, gid, B, W)
+    rng = np.random.default_rng(200 + seed)
+    for _ in range(5):
+        q = rng.integers(0, 1 << W, size=L).astype(np.uint32)
+        assert np.array_equal(O.counts(off, cells, L, W, q, B * R), O.counts_direct(buckets, gid, B, q))
