@@ -181,20 +181,29 @@ def recall_scores(c: dict, got_ids: np.ndarray, exact_ids, exact_sims) -> dict:
 # --------------------------------------------------------------------------
 
 def query_kernel_bytes(c: dict, ex: dict, counts: np.ndarray, qb: np.ndarray, kq: int) -> dict:
-    """Per-launch algorithmic bytes of the fused query kernel, following its
-    level walk exactly: query buckets L*4, table offsets L*8, bucket lists
-    2 B per cell, then for every repetition-0 cell at count >= the stopping
-    level its member range (8 B) and per member 4 B id + 2(R-1) B group ids,
-    plus k * 5 B of output."""
+    """Per-launch algorithmic bytes of the query kernel, following its level
+    walk exactly: query buckets L*4, table offsets L*8; per table either its
+    bucket list at 2 B a cell or, for a heavy slot (>= max(B*R/16, 32)
+    cells, which the library stores as a bitmap over the B*R cells too), the
+    bitmap's ceil(B*R/32)*4 B; then for every repetition-0 cell at count >= the
+    stopping level its member range (8 B) and per member its record (4 B id +
+    2(R-1) B group ids), plus k * 5 B of output."""
     R, B, L, W = c["R"], c["B"], c["L"], c["W"]
+    BR = B * R
+    heavy_min = max(BR // 16, 32)
+    bm_bytes = ((BR + 31) // 32) * 4
     gid = ex["gid"].astype(np.int64)
     off = ex["off"]
     sizes0 = np.bincount(gid[:, 0], minlength=B)
     total = 0
     members = 0
+    n_heavy = 0
     for i in range(qb.shape[0]):
         slots = (np.arange(L, dtype=np.int64) << W) | qb[i].astype(np.int64)
-        lists = int((off[slots + 1].astype(np.int64) - off[slots]).sum())
+        lens = off[slots + 1].astype(np.int64) - off[slots]
+        heavy = lens >= heavy_min
+        n_heavy += int(heavy.sum())
+        lists = int(lens[~heavy].sum()) * 2 + int(heavy.sum()) * bm_bytes
         cnt = counts[i].astype(np.int64)
         cell = gid + (np.arange(R) * B)[None, :]
         score = cnt[cell].min(axis=1)
@@ -209,8 +218,8 @@ def query_kernel_bytes(c: dict, ex: dict, counts: np.ndarray, qb: np.ndarray, kq
         enum_cells = np.nonzero(c0 >= tstop)[0]
         m = int(sizes0[enum_cells].sum())
         members += m
-        total += L * 4 + L * 8 + lists * 2 + len(enum_cells) * 8 + m * (4 + 2 * (R - 1)) + kq * 5
-    return {"bytes": total, "members": members}
+        total += L * 4 + L * 8 + lists + len(enum_cells) * 8 + m * (4 + 2 * (R - 1)) + kq * 5
+    return {"bytes": total, "members": members, "heavy_tables": n_heavy}
 
 
 def hash_kernel_bytes(c: dict) -> int:
@@ -529,7 +538,7 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     qbytes = query_kernel_bytes(c, ex, counts, qb_h[acc], k)
     scale = nq / len(acc)                          # per-query accounting on a sample, scaled
     qbytes = {"bytes": qbytes["bytes"] * scale, "members": qbytes["members"] * scale,
-              "sample": int(len(acc))}
+              "heavy": qbytes["heavy_tables"] * scale, "sample": int(len(acc))}
     hbytes = hash_kernel_bytes(c)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -574,6 +583,7 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
                      "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                      "algorithmic_bytes": "query hashing + per-query lists, enumerated members, outputs",
                      "members_enumerated_per_query": qbytes["members"] / nq,
+                     "heavy_tables_per_query": qbytes["heavy"] / nq,
                      "accounting_queries": qbytes["sample"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "api": "flinng_query, host pinned buffers"},

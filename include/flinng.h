@@ -120,6 +120,16 @@ int flinng_build(flinng_index *idx, const flinng_points *pts, uint64_t n,
                  const uint32_t *perm, int on_device);
 
 /*
+ * flinng_build from precomputed buckets (n x L uint32, as flinng_hash
+ * returns them) instead of points: Alg. 1 and the reverse index of Sec. 5
+ * over points already hashed, e.g. hashed batch by batch by the caller so
+ * that the points themselves are never held at once.
+ * Errors: as flinng_build; INVALID_ARG also for a bucket >= 2^W.
+ */
+int flinng_build_buckets(flinng_index *idx, const uint32_t *buckets, uint64_t n,
+                         const uint32_t *perm, int on_device);
+
+/*
  * Add n points with ids size .. size+n-1. Alg. 1 applied to the batch with
  * positions continuing after the current size: position i of row r of perm
  * goes to cell (r, (size + i) mod B). The reverse index becomes that of the
@@ -168,13 +178,15 @@ int flinng_set_stream(flinng_index *idx, void *stream);
  *   CTA and goes straight on to count / decode / top-k (default);
  * FLINNG_QUERY_GRAPH - the fused kernel launched through a CUDA graph kept
  *   per batch-size class (nq rounded up to a power of two); each call
- *   rewrites the graph's kernel arguments and replays it. */
+ *   rewrites the graph's kernel arguments and replays it.
+ * Cosine indices whose projection matrix has more than 2^18 entries (L*K*dim)
+ * hash every batch with the batched GEMM in all modes. */
 #define FLINNG_QUERY_PLAIN 0
 #define FLINNG_QUERY_FUSED 1
 #define FLINNG_QUERY_GRAPH 2
 int flinng_set_query_mode(flinng_index *idx, uint32_t mode);
 
-/* Autotune the fused query on a sample batch: times CTA sizes (128, 256),
+/* Autotune the fused query on a sample batch: times CTA sizes (128, 256, 512),
  * CTAs per SM and candidate-buffer sizes on this batch (synchronously) and
  * keeps the fastest for batches of the same size class (power of two of
  * nq); later fused/graph calls of that class use it. Results never depend on
@@ -269,6 +281,32 @@ uint64_t flinng_kernel_launches(void);
 int flinng_query_noalloc(flinng_index *idx, const flinng_points *q, uint32_t nq,
                          const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
                          uint8_t *out_scores);
+
+/* ---------------------------------------------------------------------- */
+/* Synthetic input (not part of FLINNG)                                    */
+/* ---------------------------------------------------------------------- */
+
+/* Embeddings streamed from a seed, shaped like the paper's YFCC100M
+ * workload (Sec. 6, Table 1: 4096-dimensional neural activations, about half
+ * zeros): ReLU of a Gaussian mixture with n_centers centres ~ N(0, I),
+ * points = ReLU(centre + sigma * z), queries = ReLU(pre-ReLU value of a
+ * random point + q_sigma * z), z from Philox4x32-10 counters through an
+ * Irwin-Hall sum of four uniforms. Any row can be regenerated alone. */
+typedef struct flinng_embed_spec {
+    uint64_t seed;
+    uint32_t dim;
+    uint32_t n_centers;
+    float sigma;
+    float q_sigma;
+    uint64_t n_points;      /* queries draw their source point from [0, n_points) */
+} flinng_embed_spec;
+
+/* Write rows first .. first+n-1 of the point stream (queries = 0) or of the
+ * query stream (queries = 1) to out (DEVICE memory, n x spec->dim, row stride
+ * ld floats), asynchronously on stream (cudaStream_t or NULL). Row indices
+ * must stay below 2^32. Errors: INVALID_ARG, CUDA. */
+int flinng_generate_embeddings(const flinng_embed_spec *spec, int queries, uint64_t first,
+                               uint64_t n, float *out, uint64_t ld, void *stream);
 
 #ifdef __cplusplus
 }

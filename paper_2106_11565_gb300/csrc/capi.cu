@@ -67,7 +67,7 @@ void free_index(flinng_index *ix)
     destroy_graphs(ix);
     void *ptrs[] = {ix->srp_w, ix->bucket_a, ix->bucket_c, ix->gid, ix->moff, ix->mem, ix->mrec, ix->off,
                     ix->hidx, ix->hbm,
-                    ix->cells, ix->cells_tmp, ix->slot_a, ix->slot_b, ix->cell_cnt, ix->flag,
+                    ix->cells, ix->cells_tmp, ix->slot_a, ix->slot_b, ix->cell_cnt, ix->flag, ix->qnext,
                     ix->stats, ix->ws.ptr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -187,8 +187,16 @@ size_t hash_ws_bytes(const flinng_index *ix, uint64_t n)
     return ix->cfg.metric == FLINNG_COSINE_SRP ? srp_workspace_bytes(ix, n) : 0;
 }
 
+// Checks buckets < 2^W on the device (sets ix->flag bit 4 otherwise).
+__global__ void k_check_buckets(const uint32_t *__restrict__ b, uint64_t n, uint32_t W, uint32_t *flag)
+{
+    for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
+         t += uint64_t(gridDim.x) * blockDim.x)
+        if (b[t] >> W) atomicOr(flag, 4u);
+}
+
 int insert_common(flinng_index *ix, const flinng_points *pts, uint64_t n, const uint32_t *perm,
-                  int on_device, bool reset)
+                  int on_device, bool reset, const uint32_t *given_buckets = nullptr)
 {
     if (!ix) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
     const uint64_t base = reset ? 0 : ix->n_points;
@@ -196,17 +204,17 @@ int insert_common(flinng_index *ix, const flinng_points *pts, uint64_t n, const 
         return set_error(FLINNG_ERR_CAPACITY, "insert: %llu + %llu points exceed capacity %llu",
                          (unsigned long long)base, (unsigned long long)n,
                          (unsigned long long)ix->cfg.capacity);
-    FL_TRY(check_points(ix, pts, n, on_device));
+    if (!given_buckets) FL_TRY(check_points(ix, pts, n, on_device));
     if (n > 0 && !perm) return set_error(FLINNG_ERR_INVALID_ARG, "insert: perm is null");
     const cudaStream_t st = ix->stream;
     const uint32_t R = ix->cfg.R, L = ix->cfg.L;
-    const size_t need = stage_bytes(ix, pts, n, on_device) + carve_bytes<uint32_t>(uint64_t(R) * n) +
+    const size_t need = (given_buckets ? 0 : stage_bytes(ix, pts, n, on_device)) + carve_bytes<uint32_t>(uint64_t(R) * n) +
                         carve_bytes<uint32_t>(n * L) + perm_check_workspace_bytes(R, n) +
                         hash_ws_bytes(ix, n) + insert_workspace_bytes(ix) + 4096;
     FL_TRY(ws_reserve(ix, need));
     Carver c(ix->ws.ptr, ix->ws.bytes);
     Staged s;
-    FL_TRY(stage_points(ix, pts, n, on_device, c, s));
+    if (!given_buckets) FL_TRY(stage_points(ix, pts, n, on_device, c, s));
     const uint32_t *dperm = perm;
     if (!on_device && n > 0) {
         uint32_t *p = c.take<uint32_t>(uint64_t(R) * n);
@@ -219,11 +227,27 @@ int insert_common(flinng_index *ix, const flinng_points *pts, uint64_t n, const 
     const size_t hb = hash_ws_bytes(ix, n);
     void *hws = c.take<char>(hb);
     void *iws = c.take<char>(insert_workspace_bytes(ix));
+    if (given_buckets) {
+        if (on_device) {
+            FL_CUDA(cudaMemcpyAsync(buckets, given_buckets, n * L * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+        } else if (n) {
+            FL_CUDA(cudaMemcpyAsync(buckets, given_buckets, n * L * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+        }
+        if (n) {
+            FL_CUDA(cudaMemsetAsync(ix->flag, 0, 4, st));
+            k_check_buckets<<<1024, 256, 0, st>>>(buckets, n * L, ix->cfg.range_bits, ix->flag);
+            count_launch();
+            FL_CUDA(cudaGetLastError());
+            FL_CUDA(cudaMemcpyAsync(ix->h_flag, ix->flag, 4, cudaMemcpyDeviceToHost, st));
+            FL_CUDA(cudaStreamSynchronize(st));
+            if (*ix->h_flag & 4u) return set_error(FLINNG_ERR_INVALID_ARG, "build_buckets: a bucket is >= 2^W");
+        }
+    }
     if (reset) {
         ix->n_points = 0;
         ix->n_cells = 0;
     }
-    FL_TRY(hash_staged(ix, s, n, buckets, nullptr, nullptr, hws, hb));
+    if (!given_buckets) FL_TRY(hash_staged(ix, s, n, buckets, nullptr, nullptr, hws, hb));
     FL_TRY(insert_hashed(ix, buckets, dperm, n, iws));
     return FLINNG_OK;
 }
@@ -281,6 +305,7 @@ int flinng_create(const flinng_config *cfg, const flinng_params *params, void *s
     ALLOC(slot_b, ix->nslot + 1);
     ALLOC(cell_cnt, size_t(ix->BR) + 1);
     ALLOC(flag, 4);
+    ALLOC(qnext, 4);
     ALLOC(stats, 2);
 #undef ALLOC
     if (rc == FLINNG_OK) {
@@ -374,7 +399,7 @@ int flinng_tune_query(flinng_index *idx, const flinng_points *q, uint32_t nq, ui
     FL_CUDA(cudaEventCreate(&e1));
     QueryTuning best{};
     float best_ms = 1e30f;
-    const uint32_t threads[] = {256, 128};
+    const uint32_t threads[] = {256, 128, 512};
     const uint32_t cps[] = {0, 4, 2};
     const uint32_t caps[] = {0, 4096, 1024};
     int rc = FLINNG_OK;
@@ -418,6 +443,13 @@ int flinng_build(flinng_index *idx, const flinng_points *pts, uint64_t n, const 
                  int on_device)
 {
     return insert_common(idx, pts, n, perm, on_device, true);
+}
+
+int flinng_build_buckets(flinng_index *idx, const uint32_t *buckets, uint64_t n, const uint32_t *perm,
+                         int on_device)
+{
+    if (n > 0 && !buckets) return set_error(FLINNG_ERR_INVALID_ARG, "build_buckets: buckets is null");
+    return insert_common(idx, nullptr, n, perm, on_device, true, buckets);
 }
 
 int flinng_insert(flinng_index *idx, const flinng_points *pts, uint64_t n, const uint32_t *perm,
@@ -487,7 +519,11 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
     FL_TRY(ws_reserve(idx, need));
     Carver c(idx->ws.ptr, idx->ws.bytes);
     uint32_t *qb = nullptr;
-    const bool fused = q && (idx->query_mode == FLINNG_QUERY_FUSED || idx->query_mode == FLINNG_QUERY_GRAPH);
+    // Per-CTA hashing reads all L*K projection rows for every query: for a
+    // large projection matrix the batched GEMM (plain form) hashes far better.
+    const bool big_srp = idx->cfg.metric == FLINNG_COSINE_SRP && uint64_t(idx->P) * idx->cfg.dim > (1ull << 18);
+    const bool fused = q && !big_srp &&
+                       (idx->query_mode == FLINNG_QUERY_FUSED || idx->query_mode == FLINNG_QUERY_GRAPH);
     Staged fs;
     if (fused) {
         FL_TRY(stage_points(idx, q, nq, on_device, c, fs));

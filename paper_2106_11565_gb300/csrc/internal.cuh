@@ -38,7 +38,7 @@ struct Workspace {
 };
 
 struct QueryTuning {
-    uint32_t threads;        // CTA size: 128 or 256 (0: 256)
+    uint32_t threads;        // CTA size: 128, 256 or 512 (0: 256)
     uint32_t ctas_per_sm;    // 0: occupancy limit
     uint32_t cap;            // candidate buffer entries; 0: default
     uint32_t valid;
@@ -113,6 +113,7 @@ struct flinng_index {
     uint32_t *slot_b;      // nslot + 1 (build scratch)
     uint32_t *cell_cnt;    // BR + 1 (build scratch)
     uint32_t *flag;        // device status word
+    uint32_t *qnext;       // query counter of the fused kernel
     uint32_t *h_flag;      // pinned host copy
     unsigned long long *stats;   // [recheck, exact]
     uint64_t last_recheck, last_exact;

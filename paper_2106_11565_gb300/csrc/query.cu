@@ -30,7 +30,7 @@ namespace flinng {
 
 namespace {
 
-constexpr int kQTmax = 256;              // largest CTA size (threads) of the query kernels
+constexpr int kQTmax = 256;              // CTA size of the plain and counts kernels
 constexpr uint64_t kKeyBits = (1ull << 56) - 1;
 
 struct QArgs {
@@ -541,6 +541,7 @@ struct HArgs {
     float gamma2, tiny;
     double gamma64;
     unsigned long long *stats;
+    uint32_t *qnext;    // next query to hand out (zeroed before each launch)
     uint32_t K;
     size_t hash_off;    // byte offset of the hash region in shared memory
 };
@@ -715,8 +716,15 @@ k_query_fused(QArgs a, HArgs h)
     extern __shared__ __align__(16) unsigned char sm[];
     const QSmem s = carve_q<NT>(sm, a.cap, a.kp);
     uint32_t *qb = reinterpret_cast<uint32_t *>(sm + h.hash_off);
-    uint32_t *hs = qb + ((a.L + 3) & ~3u);
-    for (uint32_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
+    uint32_t *qslot = qb + ((a.L + 3) & ~3u);
+    uint32_t *hs = qslot + 4;
+    // queries are handed out one at a time from a counter (zeroed before the
+    // launch), so CTAs that drew cheap queries take more of them
+    for (;;) {
+        if (threadIdx.x == 0) qslot[0] = atomicAdd(h.qnext, 1u);
+        __syncthreads();
+        const uint32_t q = qslot[0];
+        if (q >= a.nq) break;
         uint32_t kq = a.k ? a.k[q] : a.k_max;
         if (kq > a.k_max) kq = a.k_max;
         zero_query_state<NT>(a, s);
@@ -865,7 +873,7 @@ static int fused_prepare(flinng_index *ix, const FusedQuery &fq, const uint32_t 
                          uint32_t grid_for, FusedPlan *P)
 {
     const uint32_t nq = fq.nq;
-    const int NT = (tune && tune->threads == 128) ? 128 : 256;
+    const int NT = (tune && (tune->threads == 128 || tune->threads == 512)) ? int(tune->threads) : 256;
     QArgs &a = P->a;
     HArgs &h = P->h;
     a = make_args(ix, nullptr, nq);
@@ -876,7 +884,8 @@ static int fused_prepare(flinng_index *ix, const FusedQuery &fq, const uint32_t 
     h = HArgs{};
     const bool srp = ix->cfg.metric == FLINNG_COSINE_SRP;
     h.K = ix->cfg.K;
-    size_t hash_bytes = size_t((ix->cfg.L + 3) & ~3u) * 4;
+    h.qnext = ix->qnext;
+    size_t hash_bytes = size_t((ix->cfg.L + 3) & ~3u) * 4 + 16;
     if (srp) {
         h.x = fq.x;
         h.ldx = fq.ldx;
@@ -905,7 +914,8 @@ static int fused_prepare(flinng_index *ix, const FusedQuery &fq, const uint32_t 
     P->smem = qbytes + hash_bytes;
     if (P->smem > 227 * 1024)
         return set_error(FLINNG_ERR_INVALID_ARG, "fused query: %zu bytes of shared memory needed (> 227 KB)", P->smem);
-    P->fn = NT == 128 ? fused_kernel<128>(ix->rw, srp) : fused_kernel<256>(ix->rw, srp);
+    P->fn = NT == 128 ? fused_kernel<128>(ix->rw, srp)
+          : NT == 512 ? fused_kernel<512>(ix->rw, srp) : fused_kernel<256>(ix->rw, srp);
     P->threads = NT;
     if (P->smem > 48 * 1024)
         FL_CUDA(cudaFuncSetAttribute(P->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem));
@@ -932,6 +942,7 @@ int query_fused_launch(flinng_index *ix, const FusedQuery &fq, const uint32_t *k
     FL_TRY(fused_prepare(ix, fq, k, k_max, out_ids, out_scores, tune, fq.nq, &P));
     if (ix->cfg.metric == FLINNG_COSINE_SRP)
         FL_CUDA(cudaMemsetAsync(ix->stats, 0, 2 * sizeof(unsigned long long), ix->stream));
+    FL_CUDA(cudaMemsetAsync(ix->qnext, 0, sizeof(uint32_t), ix->stream));
     FL_CUDA(cudaLaunchKernel(P.fn, dim3(P.grid), dim3(P.threads), P.args, P.smem, ix->stream));
     count_launch();
     return FLINNG_OK;
@@ -962,18 +973,21 @@ int query_graph_launch(flinng_index *ix, const FusedQuery &fq, const uint32_t *k
         if (g.graph) cudaGraphDestroy(g.graph);
         g = QueryGraph{};
         FL_CUDA(cudaGraphCreate(&g.graph, 0));
-        cudaGraphNode_t dep = nullptr;
+        cudaGraphNode_t deps[2];
+        int ndep = 0;
+        cudaMemsetParams mp{};
+        mp.dst = ix->qnext;      // query counter
+        mp.value = 0;
+        mp.elementSize = 4;
+        mp.width = 1;
+        mp.height = 1;
+        FL_CUDA(cudaGraphAddMemsetNode(&deps[ndep++], g.graph, nullptr, 0, &mp));
         if (srp) {
-            cudaMemsetParams mp{};
             mp.dst = ix->stats;
-            mp.value = 0;
-            mp.elementSize = 4;
             mp.width = 4;        // 2 x 64-bit counters
-            mp.height = 1;
-            mp.pitch = 0;
-            FL_CUDA(cudaGraphAddMemsetNode(&dep, g.graph, nullptr, 0, &mp));
+            FL_CUDA(cudaGraphAddMemsetNode(&deps[ndep++], g.graph, nullptr, 0, &mp));
         }
-        FL_CUDA(cudaGraphAddKernelNode(&g.node, g.graph, dep ? &dep : nullptr, dep ? 1 : 0, &kp));
+        FL_CUDA(cudaGraphAddKernelNode(&g.node, g.graph, deps, ndep, &kp));
         FL_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
         g.fn = P.fn;
         g.smem = P.smem;

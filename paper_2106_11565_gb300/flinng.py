@@ -36,6 +36,11 @@ class flinng_params(C.Structure):
                 ("doph_seed", C.c_uint64), ("bucket_a", C.c_void_p), ("bucket_c", C.c_void_p)]
 
 
+class flinng_embed_spec(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("dim", C.c_uint32), ("n_centers", C.c_uint32),
+                ("sigma", C.c_float), ("q_sigma", C.c_float), ("n_points", C.c_uint64)]
+
+
 class flinng_points(C.Structure):
     _fields_ = [("x", C.c_void_p), ("ld", C.c_uint64), ("off", C.c_void_p),
                 ("elems", C.c_void_p)]
@@ -66,6 +71,9 @@ _SIGS = {
     "flinng_set_query_mode": (C.c_int, [C.c_void_p, C.c_uint32]),
     "flinng_tune_query": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint32, C.c_uint32,
                                     C.c_int, C.c_void_p]),
+    "flinng_build_buckets": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_int]),
+    "flinng_generate_embeddings": (C.c_int, [C.POINTER(flinng_embed_spec), C.c_int, C.c_uint64, C.c_uint64,
+                                             C.c_void_p, C.c_uint64, C.c_void_p]),
     "flinng_query_noalloc": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint32, C.c_void_p,
                                        C.c_uint32, C.c_void_p, C.c_void_p]),
 }
@@ -221,6 +229,13 @@ class Index:
         perm = perm if _is_cuda(perm) else _np(perm, np.uint32)
         _check(self.lib.flinng_build(self.h, C.byref(fp), n, _ptr(perm), dev))
 
+    def build_buckets(self, buckets, perm):
+        """Build from precomputed buckets (n x L)."""
+        dev = int(_is_cuda(buckets))
+        b = buckets if dev else _np(buckets, np.uint32)
+        perm = perm if _is_cuda(perm) else _np(perm, np.uint32)
+        _check(self.lib.flinng_build_buckets(self.h, _ptr(b), b.shape[0], _ptr(perm), dev))
+
     def insert(self, pts, perm):
         fp, n, dev, keep = self._points(pts)
         perm = perm if _is_cuda(perm) else _np(perm, np.uint32)
@@ -292,3 +307,19 @@ class Index:
         a, b = C.c_uint64(), C.c_uint64()
         _check(self.lib.flinng_hash_stats(self.h, C.byref(a), C.byref(b)))
         return int(a.value), int(b.value)
+
+
+def generate_embeddings(seed: int, dim: int, n_centers: int, sigma: float, first: int, n: int,
+                        queries: bool = False, q_sigma: float = 0.05, n_points: int = 0, out=None,
+                        stream=None):
+    """Rows [first, first+n) of the seeded embedding stream, as a CUDA tensor."""
+    import torch
+    sp = flinng_embed_spec(seed=seed, dim=dim, n_centers=n_centers, sigma=sigma,
+                           q_sigma=q_sigma, n_points=n_points)
+    if out is None:
+        out = torch.empty((n, dim), dtype=torch.float32, device="cuda")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load().flinng_generate_embeddings(C.byref(sp), int(queries), first, n, out.data_ptr(),
+                                             out.stride(0), C.c_void_p(stream)))
+    return out

@@ -256,3 +256,116 @@ def url_strings(seed: int, n: int, n_queries: int, vocab: int = 50_000,
     qsoff, qsel = _gram_csr(qbuf, qoff)
     return {"off": soff, "elems": sel, "q_off": qsoff, "q_elems": qsel, "src": src,
             "str_len": target}
+
+
+# --------------------------------------------------------------------------
+# embeddings streamed from a seed (YFCC100M-shaped): counter-based, so any
+# point can be regenerated alone, on the host here and on the device by the
+# library's generator (same definitions, implemented separately)
+# --------------------------------------------------------------------------
+
+PHILOX_M0, PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+PHILOX_W0, PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
+EMBED_STREAM = 0xC0
+_M32 = U64(0xFFFFFFFF)
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11),
+    vectorised over numpy arrays of counters; returns 4 uint32 arrays."""
+    c0, c1, c2, c3 = (np.asarray(x).astype(U64) for x in (c0, c1, c2, c3))
+    k0 = np.asarray(k0).astype(U64)
+    k1 = np.asarray(k1).astype(U64)
+    for r in range(10):
+        if r:
+            k0 = (k0 + U64(PHILOX_W0)) & _M32
+            k1 = (k1 + U64(PHILOX_W1)) & _M32
+        p0 = U64(PHILOX_M0) * c0
+        p1 = U64(PHILOX_M1) * c2
+        c0, c1, c2, c3 = (p1 >> U64(32)) ^ c1 ^ k0, p1 & _M32, (p0 >> U64(32)) ^ c3 ^ k1, p0 & _M32
+    return tuple(x.astype(U32) for x in (c0, c1, c2, c3))
+
+
+IH_SCALE = np.float32(np.sqrt(3.0) * 2.0 ** -22)
+
+
+def irwin_hall(u0, u1, u2, u3) -> np.ndarray:
+    """Approximate N(0, 1): the sum of four 22-bit uniforms (exact integer),
+    centred, times sqrt(3) * 2^-22 (one fp32 multiply)."""
+    s = sum((np.asarray(u).astype(np.int64) >> 10) for u in (u0, u1, u2, u3)) - (1 << 23)
+    return s.astype(np.float32) * IH_SCALE
+
+
+def fma_f32(a, b, c) -> np.ndarray:
+    """Correctly rounded fp32 fused multiply-add a*b + c (one rounding).
+
+    a*b is exact in fp64. s = fl64(a*b + c) and its error e (two-sum) give the
+    exact value s + e. Rounding s to fp32 is already correct unless s sits
+    exactly on a midpoint between two fp32 numbers; then the sign of e picks
+    the neighbour (e = 0: ties to even)."""
+    a = np.asarray(a, np.float32).astype(np.float64)
+    b = np.asarray(b, np.float32).astype(np.float64)
+    c = np.asarray(c, np.float32).astype(np.float64)
+    p = a * b
+    s = p + c
+    bb = s - p
+    e = (p - (s - bb)) + (c - bb)
+    r0 = s.astype(np.float32)
+    d = s - r0.astype(np.float64)
+    other = np.where(d > 0, np.nextafter(r0, np.float32(np.inf)), np.nextafter(r0, np.float32(-np.inf)))
+    tie = (d != 0) & (2 * np.abs(d) == np.abs(other.astype(np.float64) - r0.astype(np.float64)))
+    upper = np.where(d > 0, other, r0)
+    lower = np.where(d > 0, r0, other)
+    r = np.where(tie & (e > 0), upper, np.where(tie & (e < 0), lower, r0))
+    return r.astype(np.float32)
+
+
+def _key(seed: int):
+    return U64(seed & 0xFFFFFFFF), U64((seed >> 32) & 0xFFFFFFFF)
+
+
+def embed_centers(seed: int, centers: np.ndarray, dim: int) -> np.ndarray:
+    """Rows ``centers`` of the centre matrix, (len, dim) fp32 ~ N(0, 1)."""
+    k0, k1 = _key(seed)
+    c = np.asarray(centers, U64)[:, None]
+    t = np.arange(dim, dtype=U64)[None, :]
+    u = philox4x32_10(c + t * 0, t + c * 0, 0, EMBED_STREAM, k0, k1)
+    return irwin_hall(*u)
+
+
+def embed_labels(seed: int, idx: np.ndarray, n_centers: int) -> np.ndarray:
+    k0, k1 = _key(seed)
+    i = np.asarray(idx, U64)
+    return (philox4x32_10(i, 0, 1, EMBED_STREAM, k0, k1)[0] % U32(n_centers)).astype(np.int64)
+
+
+def embed_points(seed: int, idx, dim: int, n_centers: int, sigma: float,
+                 pre_relu: bool = False) -> np.ndarray:
+    """Points ``idx`` of the stream: ReLU(centre[label] + sigma * z), fp32."""
+    k0, k1 = _key(seed)
+    i = np.asarray(idx, U64)[:, None]
+    t = np.arange(dim, dtype=U64)[None, :]
+    lab = embed_labels(seed, idx, n_centers)
+    cen = embed_centers(seed, lab, dim)
+    z = irwin_hall(*philox4x32_10(i + t * 0, t + i * 0, 2, EMBED_STREAM, k0, k1))
+    pre = fma_f32(np.float32(sigma), z, cen)
+    return pre if pre_relu else np.where(pre > 0, pre, np.float32(0)).astype(np.float32)
+
+
+def embed_query_sources(seed: int, jdx, n_points: int) -> np.ndarray:
+    k0, k1 = _key(seed)
+    j = np.asarray(jdx, U64)
+    return (philox4x32_10(j, 0, 3, EMBED_STREAM, k0, k1)[0] % U32(n_points)).astype(np.int64)
+
+
+def embed_queries(seed: int, jdx, n_points: int, dim: int, n_centers: int, sigma: float,
+                  q_sigma: float) -> np.ndarray:
+    """Queries ``jdx``: ReLU(pre-ReLU value of a random point + q_sigma * z), fp32."""
+    k0, k1 = _key(seed)
+    src = embed_query_sources(seed, jdx, n_points)
+    pre = embed_points(seed, src, dim, n_centers, sigma, pre_relu=True)
+    j = np.asarray(jdx, U64)[:, None]
+    t = np.arange(dim, dtype=U64)[None, :]
+    z = irwin_hall(*philox4x32_10(j + t * 0, t + j * 0, 4, EMBED_STREAM, k0, k1))
+    q = fma_f32(np.float32(q_sigma), z, pre)
+    return np.where(q > 0, q, np.float32(0)).astype(np.float32)
