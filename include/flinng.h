@@ -191,7 +191,8 @@ int flinng_set_query_mode(flinng_index *idx, uint32_t mode);
  * keeps the fastest for batches of the same size class (power of two of
  * nq); later fused/graph calls of that class use it. Results never depend on
  * the tuning. chosen (optional, 3 entries): threads, CTAs per SM (0 = as many
- * as fit), buffer entries (0 = default). */
+ * as fit), buffer entries (0 = default); all 0 when the index's batches are
+ * hashed by the GEMM (nothing to tune). */
 int flinng_tune_query(flinng_index *idx, const flinng_points *q, uint32_t nq,
                       uint32_t k_max, int on_device, uint32_t *chosen);
 

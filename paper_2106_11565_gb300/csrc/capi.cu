@@ -382,6 +382,11 @@ int flinng_tune_query(flinng_index *idx, const flinng_points *q, uint32_t nq, ui
 {
     if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
     if (nq == 0) return set_error(FLINNG_ERR_INVALID_ARG, "tune: empty batch");
+    if (idx->cfg.metric == FLINNG_COSINE_SRP && uint64_t(idx->P) * idx->cfg.dim > (1ull << 18)) {
+        // batches of this index are hashed by the GEMM, not by the fused kernel
+        if (chosen) chosen[0] = chosen[1] = chosen[2] = 0;
+        return FLINNG_OK;
+    }
     if (k_max > kMaxKMax) return set_error(FLINNG_ERR_INVALID_ARG, "tune: k_max > %u", kMaxKMax);
     FL_TRY(check_points(idx, q, nq, on_device));
     const cudaStream_t st = idx->stream;

@@ -283,15 +283,15 @@ class Index:
         _check(self.lib.flinng_counts(self.h, _ptr(qb), qb.shape[0], _ptr(out), dev))
         return out
 
-    def export(self) -> dict:
+    def export(self, cells: bool = True) -> dict:
         nc = C.c_uint64()
         _check(self.lib.flinng_export(self.h, None, None, 0, C.byref(nc), None))
         off = np.zeros((self.L << self.W) + 1, np.uint32)
-        cells = np.zeros(max(int(nc.value), 1), np.uint16)
+        cl = np.zeros(max(int(nc.value), 1), np.uint16) if cells else None
         gid = np.zeros((max(self.size, 1), self.R), np.uint16)
-        _check(self.lib.flinng_export(self.h, off.ctypes.data, cells.ctypes.data, cells.size,
-                                      C.byref(nc), gid.ctypes.data))
-        return {"off": off, "cells": cells[: nc.value], "gid": gid[: self.size]}
+        _check(self.lib.flinng_export(self.h, off.ctypes.data, cl.ctypes.data if cells else None,
+                                      cl.size if cells else 0, C.byref(nc), gid.ctypes.data))
+        return {"off": off, "cells": cl[: nc.value] if cells else None, "gid": gid[: self.size]}
 
     def set_query_mode(self, mode: int):
         _check(self.lib.flinng_set_query_mode(self.h, mode))

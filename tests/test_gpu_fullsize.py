@@ -82,3 +82,54 @@ def test_url_strings_full_size_sampled(F):
         assert np.array_equal(gcnt[r], cnt)
         oid, osc, n = O.alg3(cnt, moff, mem, N, R, B, k)
         assert np.array_equal(u32(ids)[i], oid) and np.array_equal(sc[i], osc)
+
+
+def test_embeddings_full_size_sampled(F):
+    """10^7 x 4096 embeddings streamed from the seed: the device generator
+    against the host generator, the SRP codes of sampled points against the
+    oracle's exact signs, the group ids, and sampled queries end to end."""
+    import ctypes as C
+
+    import torch
+    seed = WL.config_seed(4)
+    N, d, nc, sig, qsig = 10_000_000, 4096, 1000, 0.1, 0.05
+    nq, R, B, L, K, k = 10_000, 3, 20000, 64, 16, 10
+    rows = np.array([0, 1, 12345, 7_654_321, N - 1])
+    for r in rows:
+        xd = F.generate_embeddings(seed, d, nc, sig, int(r), 1).cpu().numpy()
+        assert np.array_equal(xd, WL.embed_points(seed, [r], d, nc, sig))
+    qd_all = F.generate_embeddings(seed, d, nc, sig, 0, nq, queries=True, q_sigma=qsig, n_points=N)
+    qrows = np.array([0, 7, 4242, nq - 1])
+    assert np.array_equal(qd_all[torch.from_numpy(qrows).cuda()].cpu().numpy(),
+                          WL.embed_queries(seed, qrows, N, d, nc, sig, qsig))
+
+    w = WL.srp_projections(seed, L * K, d)
+    perm = WL.group_permutations(seed, R, N)
+    ix = F.Index("cosine", R, B, L, K, capacity=N, params=w, dim=d)
+    all_b = torch.empty((N, L), dtype=torch.int32, device="cuda")
+    ch = 32768
+    xbuf = torch.empty((ch, d), dtype=torch.float32, device="cuda")
+    for first in range(0, N, ch):
+        n = min(ch, N - first)
+        x = F.generate_embeddings(seed, d, nc, sig, first, n, out=xbuf[:n])
+        fp = F.flinng_points()
+        fp.x, fp.ld = x.data_ptr(), d
+        F._check(ix.lib.flinng_hash(ix.h, C.byref(fp), n, all_b[first:first + n].data_ptr(), None, None, 1))
+    ix.build_buckets(all_b, perm)
+    codes = all_b.cpu().numpy().view(np.uint32)
+    samp = np.unique(np.concatenate([[0, N - 1], np.random.default_rng(3).choice(N, 94, replace=False)]))
+    assert np.array_equal(codes[samp], O.srp_codes(WL.embed_points(seed, samp, d, nc, sig), w, L, K))
+    ogid = O.groups(perm, B)
+    assert np.array_equal(ix.export(cells=False)["gid"], ogid)
+    ids, sc = ix.query(qd_all, k)
+    moff, mem = O.members(ogid, B)
+    qs = np.array([0, 4242, nq - 1])
+    oqb = O.srp_codes(WL.embed_queries(seed, qs, N, d, nc, sig, qsig), w, L, K)
+    gqb, _, _ = ix.hash(qd_all[torch.from_numpy(qs).cuda()].contiguous())
+    assert np.array_equal(u32(gqb), oqb)
+    gcnt = ix.counts(oqb)
+    for r, i in enumerate(qs):
+        cnt = O.counts_direct(codes, ogid, B, oqb[r])
+        assert np.array_equal(gcnt[r], cnt)
+        oid, osc, n = O.alg3(cnt, moff, mem, N, R, B, k)
+        assert np.array_equal(u32(ids)[i], oid) and np.array_equal(sc.cpu().numpy()[i], osc)
