@@ -284,6 +284,76 @@ int flinng_query_noalloc(flinng_index *idx, const flinng_points *q, uint32_t nq,
                          uint8_t *out_scores);
 
 /* ---------------------------------------------------------------------- */
+/* Serving: continuous batching over several resident indices             */
+/* ---------------------------------------------------------------------- */
+
+/* The paper runs one query at a time on one core (Sec. 6); this runtime
+ * serves a stream of requests against several device-resident indices:
+ * queries that arrive are batched per index (uneven k and set sizes in one
+ * launch) and run on one of n_slots CUDA streams, each with its own staging
+ * and scratch, so batches overlap on the device; a slot takes the next batch
+ * as soon as its previous one completes. An insert runs when every batch in
+ * flight on its index has finished, in arrival order with that index's
+ * queries (later queries see the inserted points). Results equal those of
+ * flinng_query on the index as it stood when the query ran. */
+typedef struct flinng_server flinng_server;
+
+typedef struct flinng_server_config {
+    uint64_t hbm_budget;       /* device bytes the indices and the slots may hold */
+    uint32_t n_slots;          /* batches in flight at once (1..64), one stream each */
+    uint32_t max_batch;        /* queries per batch */
+    uint32_t k_max;            /* result width of every query, 1..1024 */
+    uint32_t max_batch_elems;  /* set elements staged per batch (Jaccard indices) */
+} flinng_server_config;
+
+#define FLINNG_REQ_QUERY 0
+#define FLINNG_REQ_INSERT 1
+
+typedef struct flinng_request {
+    double arrival_s;          /* seconds after the start of the replay (non-decreasing) */
+    uint32_t kind;             /* FLINNG_REQ_QUERY or FLINNG_REQ_INSERT */
+    uint32_t index;            /* id from flinng_server_add_index */
+    uint32_t k;                /* query: results wanted, <= k_max */
+    uint32_t on_device;        /* insert: 1 if *data and perm are device memory */
+    uint64_t n;                /* query: set size (Jaccard; ignored for cosine); insert: points */
+    const void *data;          /* query: dim floats or n uint32 set elements, HOST memory;
+                                  insert: a const flinng_points * */
+    const uint32_t *perm;      /* insert: R x n permutation, as flinng_insert */
+} flinng_request;
+
+typedef struct flinng_request_result {
+    double t_admit, t_start, t_done;   /* seconds after the start of the replay */
+    uint32_t status;           /* FLINNG_OK or the insert's error (CAPACITY, ...) */
+    uint32_t version;          /* inserts applied to the index when the request ran */
+    uint32_t batch;            /* queries: sequence number of the batch it ran in */
+    uint32_t reserved;
+} flinng_request_result;
+
+/* Create a server (streams and events; no index yet). */
+int flinng_server_create(const flinng_server_config *cfg, flinng_server **out);
+
+/* Register an index (created and built by the caller, not owned by the
+ * server; its stream must not be used by anyone else while the server runs).
+ * Admission by HBM budget: the index's device bytes plus the slots' scratch
+ * must fit hbm_budget with the indices already registered, else
+ * FLINNG_ERR_OOM and nothing changes. */
+int flinng_server_add_index(flinng_server *srv, flinng_index *idx, uint32_t *index_id);
+
+/* Device bytes held by the registered indices and the slots. */
+uint64_t flinng_server_device_bytes(const flinng_server *srv);
+
+/* Serve n requests, each admitted when the clock reaches its arrival time;
+ * returns when all are done. out_ids / out_scores: n x k_max (HOST), rows of
+ * queries written (padding as flinng_query), rows of inserts untouched.
+ * res: per-request times, status, index version and batch.
+ * Errors: INVALID_ARG (bad request, checked before anything runs), CUDA. */
+int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_t n,
+                         uint32_t *out_ids, uint8_t *out_scores, flinng_request_result *res);
+
+/* Destroy the server (not its indices). NULL is a no-op. */
+int flinng_server_destroy(flinng_server *srv);
+
+/* ---------------------------------------------------------------------- */
 /* Synthetic input (not part of FLINNG)                                    */
 /* ---------------------------------------------------------------------- */
 

@@ -41,6 +41,24 @@ class flinng_embed_spec(C.Structure):
                 ("sigma", C.c_float), ("q_sigma", C.c_float), ("n_points", C.c_uint64)]
 
 
+class flinng_server_config(C.Structure):
+    _fields_ = [("hbm_budget", C.c_uint64), ("n_slots", C.c_uint32), ("max_batch", C.c_uint32),
+                ("k_max", C.c_uint32), ("max_batch_elems", C.c_uint32)]
+
+
+class flinng_request(C.Structure):
+    _fields_ = [("arrival_s", C.c_double), ("kind", C.c_uint32), ("index", C.c_uint32), ("k", C.c_uint32),
+                ("on_device", C.c_uint32), ("n", C.c_uint64), ("data", C.c_void_p), ("perm", C.c_void_p)]
+
+
+class flinng_request_result(C.Structure):
+    _fields_ = [("t_admit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
+                ("status", C.c_uint32), ("version", C.c_uint32), ("batch", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+REQ_QUERY, REQ_INSERT = 0, 1
+
+
 class flinng_points(C.Structure):
     _fields_ = [("x", C.c_void_p), ("ld", C.c_uint64), ("off", C.c_void_p),
                 ("elems", C.c_void_p)]
@@ -71,6 +89,11 @@ _SIGS = {
     "flinng_set_query_mode": (C.c_int, [C.c_void_p, C.c_uint32]),
     "flinng_tune_query": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint32, C.c_uint32,
                                     C.c_int, C.c_void_p]),
+    "flinng_server_create": (C.c_int, [C.POINTER(flinng_server_config), C.POINTER(C.c_void_p)]),
+    "flinng_server_add_index": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_uint32)]),
+    "flinng_server_device_bytes": (C.c_uint64, [C.c_void_p]),
+    "flinng_server_replay": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "flinng_server_destroy": (C.c_int, [C.c_void_p]),
     "flinng_build_buckets": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_int]),
     "flinng_generate_embeddings": (C.c_int, [C.POINTER(flinng_embed_spec), C.c_int, C.c_uint64, C.c_uint64,
                                              C.c_void_p, C.c_uint64, C.c_void_p]),
@@ -323,3 +346,48 @@ def generate_embeddings(seed: int, dim: int, n_centers: int, sigma: float, first
     _check(load().flinng_generate_embeddings(C.byref(sp), int(queries), first, n, out.data_ptr(),
                                              out.stride(0), C.c_void_p(stream)))
     return out
+
+
+class Server:
+    """Continuous-batching server over several resident indices (C runtime)."""
+
+    def __init__(self, hbm_budget: int, n_slots: int = 4, max_batch: int = 1024, k_max: int = 100,
+                 max_batch_elems: int = 4 << 20):
+        self.lib = load()
+        cfg = flinng_server_config(hbm_budget=hbm_budget, n_slots=n_slots, max_batch=max_batch,
+                                   k_max=k_max, max_batch_elems=max_batch_elems)
+        h = C.c_void_p()
+        _check(self.lib.flinng_server_create(C.byref(cfg), C.byref(h)))
+        self.h, self.k_max, self.indices = h, k_max, []
+
+    def add_index(self, index: "Index") -> int:
+        i = C.c_uint32()
+        _check(self.lib.flinng_server_add_index(self.h, index.h, C.byref(i)))
+        self.indices.append(index)
+        return int(i.value)
+
+    @property
+    def device_bytes(self) -> int:
+        return int(self.lib.flinng_server_device_bytes(self.h))
+
+    def replay(self, reqs):
+        """reqs: a ctypes array of flinng_request (kept alive by the caller,
+        with every buffer it points to). Returns (ids, scores, results)."""
+        n = len(reqs)
+        ids = np.zeros((max(n, 1), self.k_max), np.uint32)
+        sc = np.zeros((max(n, 1), self.k_max), np.uint8)
+        res = (flinng_request_result * max(n, 1))()
+        _check(self.lib.flinng_server_replay(self.h, C.cast(reqs, C.c_void_p), n, ids.ctypes.data,
+                                             sc.ctypes.data, C.cast(res, C.c_void_p)))
+        return ids[:n], sc[:n], res
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.flinng_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
