@@ -22,6 +22,7 @@ Workloads (synthetic, seeded, shaped like the paper's datasets):
 from __future__ import annotations
 
 import argparse
+import ctypes as C
 import hashlib
 import json
 import os
@@ -360,8 +361,97 @@ def recorded_traffic(workload: str, kernel: str = "k_query_fused"):
 
 
 # --------------------------------------------------------------------------
+# serving form: Poisson traces replayed by the C runtime
+# --------------------------------------------------------------------------
+
+def make_trace(F, rng, rate: float, T: float, sources: list, inserts: list | None = None):
+    """Poisson arrivals at ``rate`` for ``T`` seconds. ``sources``: one dict
+    per index {"id", "kind": "sets"|"dense", "share", ...data}; k uniform in
+    {1, 10, 100}. ``inserts``: (time, index id, flinng_points, n, perm) tuples
+    merged in arrival order."""
+    n = max(1, int(rng.poisson(rate * T)))
+    t = np.sort(rng.uniform(0.0, T, size=n))
+    shares = np.array([src["share"] for src in sources], float)
+    which = rng.choice(len(sources), size=n, p=shares / shares.sum())
+    req = np.zeros(n, F.REQ_DTYPE)
+    req["arrival_s"] = t
+    req["kind"] = F.REQ_QUERY
+    req["k"] = rng.choice([1, 10, 100], size=n)
+    for si, src in enumerate(sources):
+        m = which == si
+        cnt = int(m.sum())
+        j = rng.integers(0, src["nq"], size=cnt)
+        req["index"][m] = src["id"]
+        if src["kind"] == "sets":
+            req["n"][m] = src["sizes"][j]
+            req["data"][m] = src["base"] + src["off"][j] * 4
+        else:
+            req["data"][m] = src["base"] + j.astype(np.uint64) * np.uint64(src["dim"] * 4)
+    if inserts:
+        ins = np.zeros(len(inserts), F.REQ_DTYPE)
+        for i, (ti, idx, fp, cnt, perm) in enumerate(inserts):
+            ins[i] = (ti, F.REQ_INSERT, idx, 0, 0, cnt, C.addressof(fp), perm.ctypes.data)
+        req = np.concatenate([req, ins])
+        req = req[np.argsort(req["arrival_s"], kind="stable")]
+    return np.ascontiguousarray(req)
+
+
+def trace_stats(req, res, F) -> dict:
+    q = req["kind"] == F.REQ_QUERY
+    lat = (res["t_done"] - req["arrival_s"])[q]
+    span = float(res["t_done"][q].max() - req["arrival_s"][q].min())
+    out = {"queries": int(q.sum()), "achieved_qps": float(q.sum() / span),
+           "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+           "batches": int(len(np.unique(res["batch"][q])))}
+    for idx in np.unique(req["index"][q]):
+        m = q & (req["index"] == idx)
+        li = (res["t_done"] - req["arrival_s"])[m]
+        out[f"index{int(idx)}"] = {"queries": int(m.sum()), "p50_ms": float(np.percentile(li, 50) * 1e3),
+                                   "p99_ms": float(np.percentile(li, 99) * 1e3)}
+    ins = req["kind"] == F.REQ_INSERT
+    if ins.any():
+        out["inserts"] = [{"n": int(req["n"][i]), "status": int(res["status"][i]),
+                           "ms": float((res["t_done"][i] - res["t_start"][i]) * 1e3)} for i in np.nonzero(ins)[0]]
+    return out
+
+
+def sets_source(F, idx_id, q, share, keep):
+    """Host-resident query sets (pinned) for a trace."""
+    import torch
+    qoff, qel = q
+    el = torch.from_numpy(qel.view(np.int32)).pin_memory()
+    keep.append(el)
+    return {"id": idx_id, "kind": "sets", "share": share, "nq": len(qoff) - 1,
+            "sizes": np.diff(qoff).astype(np.uint64), "off": qoff[:-1].astype(np.uint64),
+            "base": np.uint64(el.data_ptr())}
+
+
+def dense_source(F, idx_id, h_q, share, keep):
+    keep.append(h_q)
+    return {"id": idx_id, "kind": "dense", "share": share, "nq": h_q.shape[0], "dim": h_q.shape[1],
+            "base": np.uint64(h_q.ctypes.data)}
+
+
+# --------------------------------------------------------------------------
 # CPU oracle timing
 # --------------------------------------------------------------------------
+
+def build_streamed(F, ix, c: dict, dev, d_perm):
+    """Build over the seeded embedding stream: generate a chunk on the device,
+    hash it (SRP GEMM), keep its buckets; then one flinng_build_buckets."""
+    import torch
+    L = c["L"]
+    all_b = torch.empty((c["N"], L), dtype=torch.int32, device=dev)
+    xbuf = torch.empty((c["chunk"], c["d"]), dtype=torch.float32, device=dev)
+    for first in range(0, c["N"], c["chunk"]):
+        n = min(c["chunk"], c["N"] - first)
+        x = F.generate_embeddings(c["seed"], c["d"], c["n_centers"], c["sigma"], first, n, out=xbuf[:n])
+        fp = F.flinng_points()
+        fp.x, fp.ld = x.data_ptr(), c["d"]
+        F._check(ix.lib.flinng_hash(ix.h, C.byref(fp), n, all_b[first:first + n].data_ptr(), None, None, 1))
+    ix.build_buckets(all_b, d_perm)
+    del all_b, xbuf
+
 
 def oracle_index(c: dict):
     from oracle import oracle as O
@@ -428,24 +518,12 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     if c.get("embed"):
         # stream: generate a chunk on the device, hash it (SRP GEMM), keep only
         # its buckets; then one flinng_build_buckets over all points
-        import ctypes as C
         d_pts = None
         d_q = F.generate_embeddings(c["seed"], c["d"], c["n_centers"], c["sigma"], 0, nq,
                                     queries=True, q_sigma=c["qsigma"], n_points=c["N"])
         c["d_q"] = d_q
-        all_b = torch.empty((c["N"], L), dtype=torch.int32, device=dev)
-        xbuf = torch.empty((c["chunk"], c["d"]), dtype=torch.float32, device=dev)
-
         def build_once():
-            for first in range(0, c["N"], c["chunk"]):
-                n = min(c["chunk"], c["N"] - first)
-                x = F.generate_embeddings(c["seed"], c["d"], c["n_centers"], c["sigma"], first, n,
-                                          out=xbuf[:n])
-                fp = F.flinng_points()
-                fp.x, fp.ld = x.data_ptr(), c["d"]
-                F._check(ix.lib.flinng_hash(ix.h, C.byref(fp), n, all_b[first:first + n].data_ptr(),
-                                            None, None, 1))
-            ix.build_buckets(all_b, d_perm)
+            build_streamed(F, ix, c, dev, d_perm)
         n_builds, n_warm = 1, 0
         build_note = ("streamed: generate 32768-point chunks on the device, FP32 SRP GEMM, keep buckets; "
                       "then flinng_build_buckets (generation included)")
@@ -587,6 +665,32 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     e2e_value = world * nq * args.steps / e2e_total
     d2h = nq * k * 5
 
+    # ---- serving form on this index: Poisson traces through the C runtime
+    serving = None
+    if not args.no_serving and world == 1 and not c.get("embed"):
+        keep = []
+        srv = F.Server(hbm_budget=ix.device_bytes + (2 << 30), n_slots=8, max_batch=1024, k_max=max(100, k),
+                       max_batch_elems=1 << 21)
+        sid = srv.add_index(ix)
+        src = (sets_source(F, sid, c["q"], 1.0, keep) if c["metric"] != "cosine"
+               else dense_source(F, sid, torch.from_numpy(c["q"]).pin_memory().numpy(), 1.0, keep))
+        rng_t = np.random.default_rng([c["seed"], 77])
+        runs = {}
+        for f in (0.25, 0.5, 2.0):
+            rate = f * plain_value
+            T = min(0.25, 1.5e6 / rate)
+            req = make_trace(F, rng_t, rate, T, [src])
+            l0 = F.kernel_launches()
+            ids_s, sc_s, res = srv.replay(req)
+            runs[f"{f}x_plain"] = dict(trace_stats(req, res, F), offered_qps=rate, duration_s=T,
+                                       gpu_launches=int(F.kernel_launches() - l0))
+        srv.close()
+        serving = {"form": "continuous batching (C runtime, 8 streams, batches <= 1024, host buffers)",
+                   "plain_form_qps": plain_value, "runs": runs,
+                   "max_qps": runs["2.0x_plain"]["achieved_qps"],
+                   "note": "offered load relative to the plain form's device-resident throughput; the serving "
+                           "path stages every request from host memory, which bounds it at high rates"}
+
     if rank != 0:
         return None
 
@@ -672,6 +776,8 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if serving is not None:
+        line["serving"] = serving
     if not args.no_cpu_baseline and c.get("embed"):
         # the oracle cannot hold 10^7 x 4096 points: a reduced index over the
         # first 2,000 points of the same stream, 40 of the same queries
@@ -696,6 +802,131 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
         line["cpu_baseline"] = {"value": qps, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{n} queries ({n // nq} passes of the batch), {el:.1f} s, "
                                           "index built beforehand (not timed)"}
+    return line
+
+
+def run_serving(args) -> dict:
+    """C5: the genomic (C2) and embedding (C4) indices resident together,
+    Poisson query arrivals with k in {1, 10, 100} at several rates relative to
+    the plain form's throughput, insert batches of 1k-100k reads into the
+    genomic index, admission by HBM budget."""
+    import torch
+    from paper_2106_11565_gb300 import _build
+    from paper_2106_11565_gb300 import flinng as F
+    _build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    keep = []
+    c2 = make_workload("C2")
+    c4 = make_workload("C4")
+    # genomic index, room for inserts from a pool of further reads
+    pool = WL.genomic_reads(c2["seed"] + 1000, c2["ref_len"], 100_000, c2["read_len"], 1)
+    ix2 = F.Index("jaccard", c2["R"], c2["B"], c2["L"], c2["K"], capacity=c2["N"] + 400_000,
+                  params=c2["params"], W=c2["W"])
+    off2, el2 = c2["pts"]
+    d2 = (torch.from_numpy(off2.view(np.int64)).to(dev), torch.from_numpy(el2.view(np.int32)).to(dev))
+    ix2.build(d2, torch.from_numpy(c2["perm"].view(np.int32)).to(dev))
+    q2 = (torch.from_numpy(c2["q"][0].view(np.int64)).to(dev), torch.from_numpy(c2["q"][1].view(np.int32)).to(dev))
+    ix2.tune(q2, 100)
+    # embedding index (streamed build)
+    ix4 = F.Index("cosine", c4["R"], c4["B"], c4["L"], c4["K"], capacity=c4["N"], params=c4["params"],
+                  dim=c4["d"], W=c4["W"])
+    t0 = time.perf_counter()
+    build_streamed(F, ix4, c4, dev, torch.from_numpy(c4["perm"].view(np.int32)).to(dev))
+    torch.cuda.synchronize()
+    build4_s = time.perf_counter() - t0
+    q4 = F.generate_embeddings(c4["seed"], c4["d"], c4["n_centers"], c4["sigma"], 0, c4["nq"], queries=True,
+                               q_sigma=c4["qsigma"], n_points=c4["N"])
+    # plain form (hash kernel, then count/decode/top-k), device buffers, k = 100
+    plain = {}
+    rng_k = np.random.default_rng([c2["seed"], 56])
+    for name, ix, q, nq in (("C2", ix2, q2, c2["nq"]), ("C4", ix4, q4, c4["nq"])):
+        ix.set_query_mode(F.QUERY_PLAIN)
+        # the same k mix as the served traffic, per query
+        kk = torch.from_numpy(rng_k.choice([1, 10, 100], size=nq).astype(np.int32)).to(dev)
+        ix.query(q, 100, k=kk)
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ix.query(q, 100, k=kk)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ids_p, sc_p = ix.query(q, 100)        # full width, for the prefix checks below
+        torch.cuda.synchronize()
+        plain[name] = {"qps": nq / (statistics.median(ts) / 1e3), "ms_per_batch": statistics.median(ts),
+                       "ids": ids_p.cpu().numpy().view(np.uint32)}
+        ix.set_query_mode(F.QUERY_FUSED)
+    plain_mix = 2.0 / (1.0 / plain["C2"]["qps"] + 1.0 / plain["C4"]["qps"])    # 50/50 mix
+    srv = F.Server(hbm_budget=ix2.device_bytes + ix4.device_bytes + (4 << 30), n_slots=8, max_batch=1024,
+                   k_max=100, max_batch_elems=1 << 21)
+    id2 = srv.add_index(ix2)
+    id4 = srv.add_index(ix4)
+    h_q4 = q4.cpu().pin_memory().numpy()
+    sources = [sets_source(F, id2, c2["q"], 0.5, keep), dense_source(F, id4, h_q4, 0.5, keep)]
+    rng = np.random.default_rng([c2["seed"], 55])
+    poff, pel = pool["off"], pool["elems"]
+    used = 0
+    runs = {}
+    clocks = ClockSampler(0)
+    time.sleep(0.3)
+    t_load = time.time()
+    launches = 0
+    for f in (0.25, 0.5, 0.9, 2.0):
+        rate = f * plain_mix
+        T = min(1.0, 1.5e6 / rate)
+        n_ins = int(round(np.exp(rng.uniform(np.log(1e3), np.log(1e5)))))
+        n_ins = min(n_ins, len(poff) - 1)
+        lo = used % (len(poff) - 1 - n_ins + 1)
+        off = (poff[lo:lo + n_ins + 1] - poff[lo]).astype(np.uint64)
+        el = np.ascontiguousarray(pel[poff[lo]:poff[lo + n_ins]])
+        fp = F.flinng_points()
+        fp.off, fp.elems = off.ctypes.data, el.ctypes.data
+        perm = WL.group_permutations(c2["seed"], c2["R"], n_ins, batch=100 + int(f * 100))
+        keep += [off, el, fp, perm]
+        used += n_ins
+        req = make_trace(F, rng, rate, T, sources, [(T / 2, id2, fp, n_ins, perm)])
+        l0 = F.kernel_launches()
+        ids_s, sc_s, res = srv.replay(req)
+        launches = int(F.kernel_launches() - l0)
+        st = dict(trace_stats(req, res, F), offered_qps=rate, duration_s=T, gpu_launches=launches)
+        # embedding queries (no inserts into that index): served == plain prefix of length k
+        m4 = np.nonzero((req["kind"] == F.REQ_QUERY) & (req["index"] == id4))[0][:2000]
+        j4 = ((req["data"][m4] - sources[1]["base"]) // np.uint64(c4["d"] * 4)).astype(np.int64)
+        same = all(np.array_equal(ids_s[r][:req["k"][r]], plain["C4"]["ids"][j][:req["k"][r]])
+                   for r, j in zip(m4, j4))
+        st["embedding_results_equal_plain"] = bool(same)
+        runs[f"{f}x_plain"] = st
+    t_end = time.time()
+    clk = clocks.stop(t_load, t_end)
+    srv.close()
+    peak = runs["2.0x_plain"]["achieved_qps"]
+    h2d_per_q = 0.5 * float(np.mean(np.diff(c2["q"][0]))) * 4 + 0.5 * c4["d"] * 4
+    line = {
+        "metric": METRIC, "value": peak, "unit": UNIT, "n_gpus": 1, "steps": len(runs),
+        "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "mixed: u32 (MinHash index) + f32 (SRP index)",
+        "data": "synthetic (seeded; stands in for the paper's datasets)",
+        "config": {"workload": "C5: serving, indices C2 (100,000 genomic reads, MinHash) and C4 (10,000,000 x "
+                               "4096 embeddings, SRP) resident together; Poisson arrivals, 50/50 mix, k uniform "
+                               "in {1,10,100}; one insert batch of 1k-100k reads per run into the genomic index",
+                   "form": "serving: continuous batching, 8 streams, batches <= 1024, host buffers in and out",
+                   "rates": "0.25x, 0.5x, 0.9x and 2.0x (overload) of the plain form's mixed throughput",
+                   "hbm_budget_bytes": int(ix2.device_bytes + ix4.device_bytes + (4 << 30))},
+        "plain_form": {"mixed_qps": plain_mix, "C2_qps": plain["C2"]["qps"], "C4_qps": plain["C4"]["qps"],
+                       "note": "hash kernel then count/decode/top-k kernel, whole query batch of each index "
+                               "resident in HBM, per-query k uniform in {1,10,100} as served"},
+        "serving": runs,
+        "serving_vs_plain": peak / plain_mix,
+        "latency_ms": {"p50_at_0.9x": runs["0.9x_plain"]["p50_ms"], "p99_at_0.9x": runs["0.9x_plain"]["p99_ms"]},
+        "e2e": {"value": peak, "unit": UNIT, "h2d_bytes_per_step": int(h2d_per_q),
+                "d2h_bytes_per_step": 500, "note": "serving is host-to-host: per query bytes"},
+        "gpu_launches": launches,
+        "build": {"C4_streamed_build_s": build4_s},
+        "clocks": clk,
+    }
     return line
 
 
@@ -736,9 +967,10 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS) + ["C5"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-form traces")
     ap.add_argument("--no-recall", action="store_true", help="skip the exact ground truth (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -750,6 +982,10 @@ def main():
             return
         c = make_workload(args.workload)
         print(json.dumps(run_reference(args, c)), flush=True)
+        return
+    if args.workload == "C5":
+        if rank == 0:
+            print(json.dumps(run_serving(args)), flush=True)
         return
     if world > 1:
         import torch

@@ -58,6 +58,14 @@ class flinng_request_result(C.Structure):
 
 REQ_QUERY, REQ_INSERT = 0, 1
 
+# numpy mirror of flinng_request, for building long traces without ctypes loops
+REQ_DTYPE = np.dtype([("arrival_s", "<f8"), ("kind", "<u4"), ("index", "<u4"), ("k", "<u4"),
+                      ("on_device", "<u4"), ("n", "<u8"), ("data", "<u8"), ("perm", "<u8")], align=True)
+assert REQ_DTYPE.itemsize == C.sizeof(flinng_request)
+RES_DTYPE = np.dtype([("t_admit", "<f8"), ("t_start", "<f8"), ("t_done", "<f8"), ("status", "<u4"),
+                      ("version", "<u4"), ("batch", "<u4"), ("reserved", "<u4")], align=True)
+assert RES_DTYPE.itemsize == C.sizeof(flinng_request_result)
+
 
 class flinng_points(C.Structure):
     _fields_ = [("x", C.c_void_p), ("ld", C.c_uint64), ("off", C.c_void_p),
@@ -371,11 +379,19 @@ class Server:
         return int(self.lib.flinng_server_device_bytes(self.h))
 
     def replay(self, reqs):
-        """reqs: a ctypes array of flinng_request (kept alive by the caller,
-        with every buffer it points to). Returns (ids, scores, results)."""
+        """reqs: a ctypes array of flinng_request or a numpy array of
+        REQ_DTYPE (kept alive by the caller, with every buffer it points to).
+        Returns (ids, scores, results); results is a ctypes array for ctypes
+        input, a numpy array of RES_DTYPE for numpy input."""
         n = len(reqs)
         ids = np.zeros((max(n, 1), self.k_max), np.uint32)
         sc = np.zeros((max(n, 1), self.k_max), np.uint8)
+        if isinstance(reqs, np.ndarray):
+            assert reqs.dtype == REQ_DTYPE and reqs.flags.c_contiguous
+            res = np.zeros(max(n, 1), RES_DTYPE)
+            _check(self.lib.flinng_server_replay(self.h, reqs.ctypes.data, n, ids.ctypes.data,
+                                                 sc.ctypes.data, res.ctypes.data))
+            return ids[:n], sc[:n], res[:n]
         res = (flinng_request_result * max(n, 1))()
         _check(self.lib.flinng_server_replay(self.h, C.cast(reqs, C.c_void_p), n, ids.ctypes.data,
                                              sc.ctypes.data, C.cast(res, C.c_void_p)))
