@@ -51,8 +51,12 @@ extern "C" {
 #define FLINNG_COSINE_SRP 0      /* dense fp32 vectors, sign random projections */
 #define FLINNG_JACCARD_DOPH 1    /* sets of uint32, densified one-permutation MinHash */
 
-/* arithmetic of the SRP projection (cosine only) */
-#define FLINNG_PREC_FP32 0
+/* arithmetic of the SRP projection (cosine only); the sign bits are exact in
+ * every precision */
+#define FLINNG_PREC_FP32 0     /* fp32 FMA tiles; fp64 / exact re-check below a rigorous margin */
+#define FLINNG_PREC_BF16X2 1   /* tensor cores (tcgen05): each operand split into two bf16 parts,
+                                  fp32 accumulation; compensated fp32, then fp64 / exact re-check of
+                                  projections below a rigorous margin; needs dim % 8 == 0 */
 
 typedef struct flinng_config {
     uint32_t metric;        /* FLINNG_COSINE_SRP or FLINNG_JACCARD_DOPH */
@@ -66,7 +70,7 @@ typedef struct flinng_config {
                                1..30 with L * 2^W < 2^31 */
     uint32_t min_threshold; /* t_min >= 1: cells with fewer collisions never test
                                positive (Sec. 5 threshold t, relaxed by Alg. 3) */
-    uint32_t precision;     /* FLINNG_PREC_FP32 */
+    uint32_t precision;     /* FLINNG_PREC_FP32 or FLINNG_PREC_BF16X2 (cosine) */
     uint32_t reserved;
     uint64_t capacity;      /* maximum number of points, inserts included;
                                L * R * capacity < 2^32 */
@@ -240,8 +244,9 @@ int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq,
 int flinng_export(flinng_index *idx, uint32_t *off, uint16_t *cells,
                   uint64_t cells_cap, uint64_t *n_cells, uint16_t *gid);
 
-/* Counters of the last hash call: SRP projections re-checked in fp64 and
- * those that needed the exact accumulator. */
+/* Counters of the last hash call (cosine): projections the first pass (fp32
+ * FMA or tensor cores) could not decide, and those that needed the exact
+ * accumulator. */
 int flinng_hash_stats(const flinng_index *idx, uint64_t *n_recheck,
                       uint64_t *n_exact);
 

@@ -68,7 +68,7 @@ void free_index(flinng_index *ix)
     void *ptrs[] = {ix->srp_w, ix->bucket_a, ix->bucket_c, ix->gid, ix->moff, ix->mem, ix->mrec, ix->off,
                     ix->hidx, ix->hbm,
                     ix->cells, ix->cells_tmp, ix->slot_a, ix->slot_b, ix->cell_cnt, ix->flag, ix->qnext,
-                    ix->stats, ix->ws.ptr};
+                    ix->stats, ix->ws.ptr, ix->w_split, ix->w_norm, ix->tc_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ix->h_flag) cudaFreeHost(ix->h_flag);
@@ -89,8 +89,10 @@ int check_config(const flinng_config *c, const flinng_params *p)
         return set_error(FLINNG_ERR_INVALID_ARG, "create: need 1 <= W <= 30 and L*2^W < 2^31");
     if (c->min_threshold < 1 || c->min_threshold > c->L)
         return set_error(FLINNG_ERR_INVALID_ARG, "create: min_threshold must be in 1..L");
-    if (c->precision != FLINNG_PREC_FP32)
+    if (c->precision != FLINNG_PREC_FP32 && c->precision != FLINNG_PREC_BF16X2)
         return set_error(FLINNG_ERR_INVALID_ARG, "create: unsupported precision %u", c->precision);
+    if (c->precision == FLINNG_PREC_BF16X2 && (c->metric != FLINNG_COSINE_SRP || c->dim % 8 != 0))
+        return set_error(FLINNG_ERR_INVALID_ARG, "create: the tensor-core precision needs cosine and dim % 8 == 0");
     if (c->capacity < 1 || uint64_t(c->L) * c->R * c->capacity >= (1ull << 32))
         return set_error(FLINNG_ERR_INVALID_ARG, "create: need capacity >= 1 and L*R*capacity < 2^32");
     if (c->metric == FLINNG_COSINE_SRP) {
@@ -178,7 +180,7 @@ int hash_staged(flinng_index *ix, const Staged &s, uint64_t n, uint32_t *buckets
                 float *proj, void *hws, size_t hws_bytes)
 {
     if (ix->cfg.metric == FLINNG_COSINE_SRP) return srp_hash(ix, s.x, s.ld, n, buckets, proj, hws, hws_bytes);
-    FL_CUDA(cudaMemsetAsync(ix->stats, 0, 2 * sizeof(unsigned long long), ix->stream));
+    FL_CUDA(cudaMemsetAsync(ix->stats, 0, kStats * sizeof(unsigned long long), ix->stream));
     return doph_hash(ix, s.off, s.elems, n, buckets, values);
 }
 
@@ -306,7 +308,8 @@ int flinng_create(const flinng_config *cfg, const flinng_params *params, void *s
     ALLOC(cell_cnt, size_t(ix->BR) + 1);
     ALLOC(flag, 4);
     ALLOC(qnext, 4);
-    ALLOC(stats, 2);
+    ALLOC(stats, kStats);
+    ALLOC(tc_err, 4);
 #undef ALLOC
     if (rc == FLINNG_OK) {
         cudaError_t e = cudaMallocHost((void **)&ix->h_flag, 16);
@@ -337,7 +340,8 @@ int flinng_create(const flinng_config *cfg, const flinng_params *params, void *s
         chk(cudaMemsetAsync(ix->off, 0, (ix->nslot + 1) * sizeof(uint32_t), st), "zero off");
         chk(cudaMemsetAsync(ix->hidx, 0xFF, (ix->nslot + 1) * sizeof(uint32_t), st), "clear hidx");
         chk(cudaMemsetAsync(ix->moff, 0, (size_t(ix->BR) + 1) * sizeof(uint32_t), st), "zero moff");
-        chk(cudaMemsetAsync(ix->stats, 0, 2 * sizeof(unsigned long long), st), "zero stats");
+        chk(cudaMemsetAsync(ix->stats, 0, kStats * sizeof(unsigned long long), st), "zero stats");
+        if (rc == FLINNG_OK && cfg->precision == FLINNG_PREC_BF16X2) rc = srp_tc_prepare_weights(ix);
         chk(cudaStreamSynchronize(st), "create sync");
     }
     if (rc != FLINNG_OK) {
@@ -644,7 +648,7 @@ int flinng_hash_stats(const flinng_index *idx, uint64_t *n_recheck, uint64_t *n_
     if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
     unsigned long long h[2] = {0, 0};
     FL_CUDA(cudaStreamSynchronize(idx->stream));
-    FL_CUDA(cudaMemcpy(h, idx->stats, sizeof h, cudaMemcpyDeviceToHost));
+    FL_CUDA(cudaMemcpy(h, idx->stats, sizeof h, cudaMemcpyDeviceToHost));   // [0] undecided, [1] exact
     if (n_recheck) *n_recheck = h[0];
     if (n_exact) *n_exact = h[1];
     return FLINNG_OK;

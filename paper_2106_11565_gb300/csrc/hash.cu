@@ -185,9 +185,14 @@ __global__ void k_srp_recheck(const float *__restrict__ X, uint64_t ldx,
         }
         if (lane == 0) {
             if (positive) atomicOr(&codes[gr * L + gc / K], 1u << (gc % K));
-            atomicAdd(&stats[0], 1ull);
+            atomicAdd(&stats[2], 1ull);
         }
     }
+}
+
+__global__ void k_add_counter(unsigned long long *dst, const unsigned long long *src)
+{
+    *dst += *src;
 }
 
 // ------------------------------------------------------------------ DOPH
@@ -265,8 +270,27 @@ k_doph(const uint64_t *__restrict__ off, const uint32_t *__restrict__ elems,
 
 }  // namespace
 
+int add_counter(unsigned long long *dst, const unsigned long long *src, cudaStream_t st)
+{
+    k_add_counter<<<1, 1, 0, st>>>(dst, src);
+    count_launch();
+    FL_CUDA(cudaGetLastError());
+    return FLINNG_OK;
+}
+
+int srp_recheck_list(flinng_index *ix, const float *x, uint64_t ld, const unsigned long long *list,
+                     const unsigned long long *count, uint32_t *codes)
+{
+    k_srp_recheck<<<152 * 4, 256, 0, ix->stream>>>(x, ld, ix->srp_w, ix->cfg.dim, ix->cfg.L, ix->cfg.K,
+                                                   ix->srp_gamma64, list, count, codes, ix->stats);
+    count_launch();
+    FL_CUDA(cudaGetLastError());
+    return FLINNG_OK;
+}
+
 size_t srp_workspace_bytes(const flinng_index *ix, uint64_t n)
 {
+    if (ix->cfg.precision == FLINNG_PREC_BF16X2) return srp_tc_workspace_bytes(ix, n);
     const uint64_t rows = n < uint64_t(kSrpChunkRows) ? n : uint64_t(kSrpChunkRows);
     return carve_bytes<unsigned long long>(2) + carve_bytes<unsigned long long>(rows * ix->P + 1);
 }
@@ -275,12 +299,13 @@ int srp_hash(flinng_index *ix, const float *x, uint64_t ld, uint64_t n,
              uint32_t *buckets, float *proj, void *ws, size_t ws_bytes)
 {
     (void)ws_bytes;
+    if (ix->cfg.precision == FLINNG_PREC_BF16X2) return srp_hash_tc(ix, x, ld, n, buckets, proj, ws);
     const cudaStream_t st = ix->stream;
     const uint32_t L = ix->cfg.L, K = ix->cfg.K, d = ix->cfg.dim, P = ix->P;
     Carver c(ws, ~size_t(0));
     unsigned long long *rcount = c.take<unsigned long long>(2);
     unsigned long long *rlist = c.take<unsigned long long>(uint64_t(kSrpChunkRows) * P + 1);
-    FL_CUDA(cudaMemsetAsync(ix->stats, 0, 2 * sizeof(unsigned long long), st));
+    FL_CUDA(cudaMemsetAsync(ix->stats, 0, kStats * sizeof(unsigned long long), st));
     if (n == 0) return FLINNG_OK;
     FL_CUDA(cudaMemsetAsync(buckets, 0, n * L * sizeof(uint32_t), st));
     // fp32 bound: 2 * gamma_d * sum|w x| + d * 2^-146 (underflow), see header comment
@@ -294,6 +319,7 @@ int srp_hash(flinng_index *ix, const float *x, uint64_t ld, uint64_t n,
                                                  proj ? proj + r0 * P : nullptr, rlist, rcount);
         count_launch();
         FL_CUDA(cudaGetLastError());
+        FL_TRY(add_counter(ix->stats, rcount, st));        // undecided after the fp32 pass
         k_srp_recheck<<<152 * 4, 256, 0, st>>>(x + r0 * ld, ld, ix->srp_w, d, L, K, ix->srp_gamma64,
                                                rlist, rcount, buckets + r0 * L, ix->stats);
         count_launch();

@@ -13,6 +13,9 @@ constexpr uint32_t kEmpty32 = 0xFFFFFFFFu;
 constexpr uint64_t kKeyNone = ~0ull;
 constexpr uint32_t kMaxKMax = 1024;
 constexpr uint32_t kDophMaxAttempts = 4096;
+// hash counters: [0] undecided after the first pass, [1] exact accumulator,
+// [2] fp64 re-checks, [3] compensated fp32 re-checks
+constexpr int kStats = 4;
 
 // Error plumbing: every internal step returns an int status and leaves a
 // message in the thread-local buffer.
@@ -84,6 +87,9 @@ struct flinng_index {
     uint64_t doph_seed;
     float srp_margin_gamma;   // 2 * gamma_d in fp32, rounded up
     double srp_gamma64;       // 2 * gamma_d for the fp64 recheck
+    void *w_split;            // tensor-core precision: bf16 w1 then w2, P x dim each
+    float *w_norm;            // upper bounds of ||w_j||
+    uint32_t *tc_err;         // tensor-core pipeline timeout flag
 
     // shape
     uint32_t P;            // L * K projections / MinHash values per point
@@ -146,6 +152,16 @@ int srp_hash(flinng_index *ix, const float *x, uint64_t ld, uint64_t n,
 // DOPH + bucket combine: buckets n x L; values (optional) n x P.
 int doph_hash(flinng_index *ix, const uint64_t *off, const uint32_t *elems,
               uint64_t n, uint32_t *buckets, uint32_t *values);
+// fp64 / exact re-check of listed (row << 20 | projection) entries
+int srp_recheck_list(flinng_index *ix, const float *x, uint64_t ld, const unsigned long long *list,
+                     const unsigned long long *count, uint32_t *codes);
+int add_counter(unsigned long long *dst, const unsigned long long *src, cudaStream_t st);
+
+// ---- srp_tc.cu (tensor-core precision form)
+int srp_tc_prepare_weights(flinng_index *ix);
+size_t srp_tc_workspace_bytes(const flinng_index *ix, uint64_t n);
+int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint32_t *buckets, float *proj,
+                void *ws);
 
 // ---- build.cu
 size_t perm_check_workspace_bytes(uint32_t R, uint64_t n);

@@ -702,7 +702,10 @@ __device__ void cta_srp(const QArgs &a, const HArgs &h, uint32_t q, uint32_t *qb
                 positive = warp_exact_sign(xs, wj, h.d, lane) > 0;
                 if (lane == 0) atomicAdd(&h.stats[1], 1ull);
             }
-            if (lane == 0) atomicAdd(&h.stats[0], 1ull);
+            if (lane == 0) {
+                atomicAdd(&h.stats[0], 1ull);
+                atomicAdd(&h.stats[2], 1ull);
+            }
         }
         if (lane == 0 && positive) atomicOr(&qb[j / h.K], 1u << (j % h.K));
     }
@@ -941,7 +944,7 @@ int query_fused_launch(flinng_index *ix, const FusedQuery &fq, const uint32_t *k
     FusedPlan P;
     FL_TRY(fused_prepare(ix, fq, k, k_max, out_ids, out_scores, tune, fq.nq, &P));
     if (ix->cfg.metric == FLINNG_COSINE_SRP)
-        FL_CUDA(cudaMemsetAsync(ix->stats, 0, 2 * sizeof(unsigned long long), ix->stream));
+        FL_CUDA(cudaMemsetAsync(ix->stats, 0, kStats * sizeof(unsigned long long), ix->stream));
     FL_CUDA(cudaMemsetAsync(ix->qnext, 0, sizeof(uint32_t), ix->stream));
     FL_CUDA(cudaLaunchKernel(P.fn, dim3(P.grid), dim3(P.threads), P.args, P.smem, ix->stream));
     count_launch();
@@ -984,7 +987,7 @@ int query_graph_launch(flinng_index *ix, const FusedQuery &fq, const uint32_t *k
         FL_CUDA(cudaGraphAddMemsetNode(&deps[ndep++], g.graph, nullptr, 0, &mp));
         if (srp) {
             mp.dst = ix->stats;
-            mp.width = 4;        // 2 x 64-bit counters
+            mp.width = 2 * kStats;   // 64-bit counters
             FL_CUDA(cudaGraphAddMemsetNode(&deps[ndep++], g.graph, nullptr, 0, &mp));
         }
         FL_CUDA(cudaGraphAddKernelNode(&g.node, g.graph, deps, ndep, &kp));

@@ -79,14 +79,15 @@ Layout layout_for(const flinng_server *srv)
     const uint64_t nb = srv->cfg.max_batch, km = srv->cfg.k_max;
     Layout L{};
     Carver c(nullptr, ~size_t(0));
-    c.take<unsigned long long>(4);                                  // query counter, stats
+    c.take<unsigned long long>(8);                                  // query counter, 4 hash counters
     L.k = (size_t)c.take<uint32_t>(nb);
     const uint64_t in_floats = nb * uint64_t(srv->max_dim);
     const uint64_t in_elems = uint64_t(srv->cfg.max_batch_elems);
     L.in_off = (size_t)c.take<uint64_t>(nb + 1);
     L.in_el = (size_t)c.take<uint32_t>(in_floats > in_elems ? in_floats : in_elems);
     L.qb = (size_t)c.take<uint32_t>(nb * srv->max_L);
-    L.srp = (size_t)c.take<unsigned long long>(nb * srv->max_P + 64);   // counter block + list
+    // re-check lists (fp32 path) or the tensor-core split operands and lists
+    L.srp = (size_t)c.take<unsigned long long>(2 * nb * srv->max_P + 64 + nb * srv->max_dim / 2 + nb + 1024);
     L.ids = (size_t)c.take<uint32_t>(nb * km);
     L.sc = (size_t)c.take<uint8_t>(nb * km);
     L.total = c.used + 256;
@@ -167,7 +168,7 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
     if (big_srp) {
         uint32_t *qb = reinterpret_cast<uint32_t *>(d + Lo.qb);
         rc = srp_hash(ix, reinterpret_cast<const float *>(d + Lo.in_el), ix->cfg.dim, nb, qb, nullptr, d + Lo.srp,
-                      (size_t(nb) * ix->P + 64) * 8);
+                      (2 * size_t(nb) * ix->P + 64) * 8);
         if (rc == FLINNG_OK) rc = query_launch(ix, qb, nb, dk, km, dids, dsc);
     } else {
         FusedQuery fq{nb, reinterpret_cast<const float *>(d + Lo.in_el), ix->cfg.dim,

@@ -1,0 +1,529 @@
+// Sign random projections on the tensor cores (the precision form): the
+// dense contraction P = X W^T runs on tcgen05 with BF16 operands and FP32
+// accumulation in tensor memory, and the sign bits stay exact.
+//
+// Exactness. Each fp32 operand is split exactly enough: x1 = bf16(x),
+// x2 = bf16(x - x1), so |x - x1 - x2| <= 2^-16 |x| (bf16 keeps 8 significant
+// bits); likewise w. bf16 x bf16 products are exact in fp32. The tile
+// computes hi = sum x1 w1 and lo = sum (x1 w2 + x2 w1) in two TMEM
+// accumulators; p~ = hi + lo differs from the exact w.x by at most
+//   (g(d) + 2^-7 g(2d) + 3.1 * 2^-16) (1 + 2^-8)^2 ||x|| ||w|| + 2^-23 |p~| + d 2^-130
+// with g(n) = n u' / (1 - n u'), u' = 2^-22: four units of fp32 rounding per
+// accumulation step, which also covers a truncating tensor-core adder.
+// Projections whose |p~| does not clear that margin go to a compensated fp32
+// re-check (two-product, two-sum), and the few that stay ambiguous to the
+// fp64 / exact re-check of hash.cu.
+//
+// Kernel layout (one CTA per 128 points x 128 projections, 192 threads):
+//   warp 0     TMA producer: 3-stage ring of {X1, X2, W1, W2} tiles of 128 rows
+//              x 64 bf16 (128-byte swizzle), one mbarrier per stage;
+//   warp 1     allocates 256 TMEM columns, one elected thread issues the MMAs
+//              (M=128, N=128, K=16) and commits each stage back to the producer;
+//   warps 2-5  epilogue: each reads its 32 TMEM lanes (one point per thread),
+//              decides the signs, writes the codes, lists ambiguous projections.
+// Every wait on an mbarrier is bounded; on timeout the CTA sets an error flag,
+// stops issuing work, waits (bounded) for the copies it issued and frees TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace flinng {
+namespace {
+
+constexpr int kTM = 128, kTN = 128, kTK = 64;     // tile rows, projections, K per stage
+constexpr int kStages = 3;
+constexpr int kTileBytes = kTM * kTK * 2;         // 16 KB per operand tile
+constexpr int kStageBytes = 4 * kTileBytes;       // X1, X2, W1, W2
+constexpr uint32_t kTmemCols = 256;               // hi: cols [0,128), lo: [128,256)
+constexpr uint64_t kWaitNs = 1000000000ull;       // bounded mbarrier waits: 1 s
+constexpr uint64_t kTcChunkRows = 16384;          // rows split and hashed per launch
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: false if the phase has not completed within kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 256; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= uint64_t((addr & 0x3FFFFu) >> 4);
+    d |= uint64_t(1) << 16;                 // leading byte offset (unused with 128B swizzle, K-major)
+    d |= uint64_t(1024 >> 4) << 32;         // stride byte offset
+    d |= uint64_t(1) << 46;                 // version
+    d |= uint64_t(2) << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major.
+__host__ __device__ constexpr uint32_t mma_idesc()
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kTN >> 3) << 17) | (uint32_t(kTM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(mma_idesc()), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcArgs {
+    uint64_t n;            // rows (points) in this launch
+    uint32_t P, d, L, K;
+    const float *xnorm;    // n: upper bounds of ||x||
+    const float *wnorm;    // P: upper bounds of ||w||
+    float c_norm;          // margin factor on ||x|| ||w||
+    float tiny;
+    uint32_t *codes;       // n x L (zeroed)
+    float *proj;           // optional n x P
+    unsigned long long *rlist;
+    unsigned long long *rcount;
+    uint32_t *err;         // set to 1 on a wait timeout
+};
+
+__global__ void __launch_bounds__(192, 1)
+k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtensorMap mx2,
+         const __grid_constant__ CUtensorMap mw1, const __grid_constant__ CUtensorMap mw2, TcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    // 1024-byte aligned tile ring, then barriers and the TMEM address
+    unsigned char *ring = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
+    uint64_t *full = reinterpret_cast<uint64_t *>(ring + kStages * kStageBytes);
+    uint64_t *empty = full + kStages;
+    uint64_t *accd = empty + kStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accd + 1);
+    uint32_t *abort_flag = tmem_slot + 1;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t row0 = blockIdx.x * kTM, col0 = blockIdx.y * kTN;
+    const uint32_t nkb = (a.d + kTK - 1) / kTK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accd, 1);
+        *abort_flag = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    uint32_t issued = 0;   // producer: k-blocks whose copies were issued
+    if (warp == 0) {
+        if (lane == 0) {
+            for (uint32_t kb = 0; kb < nkb; ++kb) {
+                const int s = kb % kStages;
+                if (kb >= uint32_t(kStages) && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) {
+                    atomicExch(abort_flag, 1u);
+                    break;
+                }
+                if (*(volatile uint32_t *)abort_flag) break;
+                unsigned char *st = ring + s * kStageBytes;
+                mbar_expect_tx(&full[s], kStageBytes);
+                const int kx = int(kb * kTK);
+                tma_load_2d(st + 0 * kTileBytes, &mx1, &full[s], kx, int(row0));
+                tma_load_2d(st + 1 * kTileBytes, &mx2, &full[s], kx, int(row0));
+                tma_load_2d(st + 2 * kTileBytes, &mw1, &full[s], kx, int(col0));
+                tma_load_2d(st + 3 * kTileBytes, &mw2, &full[s], kx, int(col0));
+                issued = kb + 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t t_hi = tmem, t_lo = tmem + kTN;
+            for (uint32_t kb = 0; kb < nkb; ++kb) {
+                const int s = kb % kStages;
+                if (!mbar_wait(&full[s], (kb / kStages) & 1)) {
+                    atomicExch(abort_flag, 1u);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t st = smem_u32(ring + s * kStageBytes);
+#pragma unroll
+                for (int kk = 0; kk < kTK / 16; ++kk) {
+                    const uint32_t off = kk * 32;
+                    const uint64_t x1 = smem_desc(st + 0 * kTileBytes + off);
+                    const uint64_t x2 = smem_desc(st + 1 * kTileBytes + off);
+                    const uint64_t w1 = smem_desc(st + 2 * kTileBytes + off);
+                    const uint64_t w2 = smem_desc(st + 3 * kTileBytes + off);
+                    const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                    mma_bf16(t_hi, x1, w1, acc);
+                    mma_bf16(t_lo, x1, w2, acc);
+                    mma_bf16(t_lo, x2, w1, 1u);
+                }
+                mma_commit(&empty[s]);
+            }
+            mma_commit(accd);      // arrives once every MMA issued above has completed
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes [32 (w % 4), +32): one point per thread
+        const uint32_t quarter = (warp & 3) * 32;
+        uint32_t got = 0;
+        if (lane == 0) got = mbar_wait(accd, 0) ? 1u : 0u;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!got && lane == 0) atomicExch(abort_flag, 1u);
+        uint32_t ab = lane == 0 ? *(volatile uint32_t *)abort_flag : 0u;
+        const bool abort = __shfl_sync(0xffffffffu, ab, 0) != 0u;   // warp-uniform
+        const uint64_t row = uint64_t(row0) + quarter + lane;
+        const bool row_ok = row < a.n && !abort;
+        const float xn = row_ok ? a.xnorm[row] : 0.f;
+        for (uint32_t c0 = 0; c0 < uint32_t(kTN) && !abort; c0 += 16) {
+            float hi[16], lo[16];
+            __syncwarp();          // the TMEM loads below are warp-collective
+            tmem_ld16(tmem + (quarter << 16) + c0, hi);
+            tmem_ld16(tmem + (quarter << 16) + kTN + c0, lo);
+            if (!row_ok) continue;
+            uint32_t cur_l = 0xFFFFFFFFu, cur_bits = 0u;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const uint32_t col = col0 + c0 + j;
+                if (col >= a.P) continue;
+                const float p = hi[j] + lo[j];
+                if (a.proj) a.proj[row * a.P + col] = p;
+                const float margin = fmaf(a.c_norm * xn, a.wnorm[col], fmaf(ldexpf(1.f, -23), fabsf(p), a.tiny));
+                if (fabsf(p) > margin) {
+                    if (p > 0.f) {
+                        const uint32_t l = col / a.K;
+                        if (l != cur_l) {
+                            if (cur_bits) atomicOr(&a.codes[row * a.L + cur_l], cur_bits);
+                            cur_l = l;
+                            cur_bits = 0u;
+                        }
+                        cur_bits |= 1u << (col % a.K);
+                    }
+                } else {
+                    const unsigned long long slot = atomicAdd(a.rcount, 1ull);
+                    a.rlist[slot] = ((unsigned long long)row << 20) | col;
+                }
+            }
+            if (cur_bits) atomicOr(&a.codes[row * a.L + cur_l], cur_bits);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (*(volatile uint32_t *)abort_flag) {
+        if (threadIdx.x == 0) atomicExch(a.err, 1u);
+        // let the copies this CTA issued land before its shared memory goes away
+        if (warp == 0 && lane == 0) {
+            for (uint32_t kb = (issued > uint32_t(kStages) ? issued - kStages : 0); kb < issued; ++kb)
+                mbar_wait(&full[kb % kStages], (kb / kStages) & 1);
+        }
+        __syncthreads();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+// x -> (bf16(x), bf16(x - bf16(x))) and an upper bound of each row's norm
+__global__ void k_split_rows(const float *__restrict__ x, uint64_t ld, uint64_t n, uint32_t d,
+                             __nv_bfloat16 *__restrict__ x1, __nv_bfloat16 *__restrict__ x2,
+                             float *__restrict__ norm)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t gw = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t r = gw; r < n; r += nw) {
+        double ss = 0.0;
+        for (uint32_t t = lane; t < d; t += 32) {
+            const float v = x[r * ld + t];
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+            x1[r * d + t] = h;
+            x2[r * d + t] = l;
+            ss += double(v) * double(v);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        // fp64 sum of d squares, sqrt, rounded up with room to spare
+        if (lane == 0) norm[r] = __double2float_ru(sqrt(ss * (1.0 + 1e-12)) * (1.0 + 1e-7));
+    }
+}
+
+// Compensated fp32 re-check of listed projections: two-product and two-sum
+// per term (one warp per projection), error at most 2^-23 |p| + 2 g(2d)^2 S
+// with S = sum |w x|. Decided bits are set; the rest go to the next list.
+__global__ void k_srp_recheck2(const float *__restrict__ X, uint64_t ldx, const float *__restrict__ Wm, uint32_t d,
+                               uint32_t L, uint32_t K, float g2, float tiny,
+                               const unsigned long long *__restrict__ rlist,
+                               const unsigned long long *__restrict__ rcount, uint32_t *__restrict__ codes,
+                               unsigned long long *__restrict__ out_list, unsigned long long *__restrict__ out_count,
+                               unsigned long long *__restrict__ stats)   // stats: compensated re-check counter
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nlist = *rcount;
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+         e < nlist; e += nwarps) {
+        const unsigned long long ent = rlist[e];
+        const uint64_t gr = ent >> 20;
+        const uint32_t gc = uint32_t(ent & 0xFFFFF);
+        const float *xr = X + gr * ldx;
+        const float *wr = Wm + uint64_t(gc) * d;
+        float s = 0.f, c = 0.f, sa = 0.f;
+        for (uint32_t t = lane; t < d; t += 32) {
+            const float xv = xr[t], wv = wr[t];
+            const float h = xv * wv;
+            const float l = fmaf(xv, wv, -h);          // exact product error
+            const float sn = s + h;                     // two-sum
+            const float z = sn - s;
+            c += (s - (sn - z)) + (h - z) + l;
+            s = sn;
+            sa = fmaf(fabsf(xv), fabsf(wv), sa);
+        }
+        // combine the lanes: lane 0 adds the 32 (s, c) pairs with two-sums
+        float ts = 0.f, tc = 0.f;
+        for (int k = 0; k < 32; ++k) {
+            const float sk = __shfl_sync(0xffffffffu, s, k);
+            const float ck = __shfl_sync(0xffffffffu, c, k);
+            const float sn = ts + sk;
+            const float z = sn - ts;
+            tc += (ts - (sn - z)) + (sk - z) + ck;
+            ts = sn;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sa = __shfl_sync(0xffffffffu, sa, 0);
+        const float p = ts + tc;
+        const float margin = fmaf(ldexpf(1.f, -23), fabsf(p), fmaf(g2, sa, tiny));
+        if (lane == 0) {
+            if (fabsf(p) > margin) {
+                if (p > 0.f) atomicOr(&codes[gr * L + gc / K], 1u << (gc % K));
+            } else {
+                out_list[atomicAdd(out_count, 1ull)] = ent;
+            }
+            atomicAdd(stats, 1ull);
+        }
+    }
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int get_encoder(EncodeTiled *fn)
+{
+    static EncodeTiled cached = nullptr;
+    if (!cached) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        FL_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        if (!p || q != cudaDriverEntryPointSuccess)
+            return set_error(FLINNG_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        cached = reinterpret_cast<EncodeTiled>(p);
+    }
+    *fn = cached;
+    return FLINNG_OK;
+}
+
+// 2-D bf16 map over rows x d (d contiguous, row stride d elements), box 64 x 128.
+int make_map(CUtensorMap *m, const void *base, uint64_t rows, uint32_t d)
+{
+    EncodeTiled enc = nullptr;
+    FL_TRY(get_encoder(&enc));
+    const cuuint64_t dims[2] = {d, rows};
+    const cuuint64_t strides[1] = {uint64_t(d) * 2};
+    const cuuint32_t box[2] = {uint32_t(kTK), uint32_t(kTM)};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(FLINNG_ERR_INVALID_ARG, "tensor map: error %d (d=%u)", int(r), d);
+    return FLINNG_OK;
+}
+
+inline unsigned warp_grid(uint64_t items)
+{
+    uint64_t b = (items * 32 + 255) / 256;
+    if (b > 152ull * 32) b = 152ull * 32;
+    return (unsigned)(b ? b : 1);
+}
+
+}  // namespace
+
+int srp_tc_prepare_weights(flinng_index *ix)
+{
+    const uint32_t P = ix->P, d = ix->cfg.dim;
+    if (d % 8 != 0) return set_error(FLINNG_ERR_INVALID_ARG, "BF16 tensor-core SRP needs dim to be a multiple of 8");
+    FL_CUDA(cudaMalloc(&ix->w_split, size_t(P) * d * 2 * sizeof(__nv_bfloat16)));
+    FL_CUDA(cudaMalloc(&ix->w_norm, size_t(P) * sizeof(float)));
+    ix->device_bytes += size_t(P) * d * 4 + size_t(P) * 4;
+    __nv_bfloat16 *w1 = static_cast<__nv_bfloat16 *>(ix->w_split);
+    k_split_rows<<<warp_grid(P), 256, 0, ix->stream>>>(ix->srp_w, d, P, d, w1, w1 + size_t(P) * d, ix->w_norm);
+    count_launch();
+    FL_CUDA(cudaGetLastError());
+    return FLINNG_OK;
+}
+
+size_t srp_tc_workspace_bytes(const flinng_index *ix, uint64_t n)
+{
+    const uint64_t rows = n < kTcChunkRows ? n : kTcChunkRows;
+    return carve_bytes<__nv_bfloat16>(rows * ix->cfg.dim * 2) + carve_bytes<float>(rows) +
+           carve_bytes<unsigned long long>(8) + 2 * carve_bytes<unsigned long long>(rows * ix->P + 1) + 4096;
+}
+
+// Codes of n rows of x (stride ld) on the tensor cores; same contract as srp_hash.
+int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint32_t *buckets, float *proj,
+                void *ws)
+{
+    const cudaStream_t st = ix->stream;
+    const uint32_t L = ix->cfg.L, K = ix->cfg.K, d = ix->cfg.dim, P = ix->P;
+    const uint64_t chunk = kTcChunkRows;
+    const uint64_t cap = n < chunk ? n : chunk;     // rows the workspace was sized for
+    Carver c(ws, ~size_t(0));
+    __nv_bfloat16 *xs = c.take<__nv_bfloat16>(cap * d * 2);
+    float *xn = c.take<float>(cap);
+    unsigned long long *cnt = c.take<unsigned long long>(8);
+    unsigned long long *list1 = c.take<unsigned long long>(cap * P + 1);
+    unsigned long long *list2 = c.take<unsigned long long>(cap * P + 1);
+    FL_CUDA(cudaMemsetAsync(ix->stats, 0, kStats * sizeof(unsigned long long), st));
+    if (n == 0) return FLINNG_OK;
+    FL_CUDA(cudaMemsetAsync(buckets, 0, n * L * sizeof(uint32_t), st));
+    FL_CUDA(cudaMemsetAsync(ix->tc_err, 0, 4, st));
+    const __nv_bfloat16 *w1 = static_cast<const __nv_bfloat16 *>(ix->w_split);
+    CUtensorMap mw1, mw2;
+    FL_TRY(make_map(&mw1, w1, P, d));
+    FL_TRY(make_map(&mw2, w1 + size_t(P) * d, P, d));
+    // margin factor (see the header comment), in double then rounded up
+    const double up = std::ldexp(1.0, -22);
+    auto g = [&](double m) { return m * up / (1.0 - m * up); };
+    const double f = (g(d) + std::ldexp(1.0, -7) * g(2.0 * d) + 3.1 * std::ldexp(1.0, -16)) *
+                     (1 + std::ldexp(1.0, -8)) * (1 + std::ldexp(1.0, -8));
+    const float c_norm = std::nextafter(float(f * 1.0001), INFINITY);
+    const float tiny = float(d) * std::ldexp(1.0f, -126);
+    const double g2d = 2.0 * d * std::ldexp(1.0, -24) / (1.0 - 2.0 * d * std::ldexp(1.0, -24));
+    const float g2 = std::nextafter(float(2.0 * g2d * g2d + std::ldexp(1.0, -40)), INFINITY);
+    const size_t smem = size_t(kStages) * kStageBytes + 1024 + 256;
+    FL_CUDA(cudaFuncSetAttribute(k_srp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (uint64_t r0 = 0; r0 < n; r0 += chunk) {
+        const uint64_t rows = (n - r0) < chunk ? (n - r0) : chunk;
+        k_split_rows<<<warp_grid(rows), 256, 0, st>>>(x + r0 * ld, ld, rows, d, xs, xs + rows * d, xn);
+        count_launch();
+        FL_CUDA(cudaGetLastError());
+        CUtensorMap mx1, mx2;
+        FL_TRY(make_map(&mx1, xs, rows, d));
+        FL_TRY(make_map(&mx2, xs + rows * d, rows, d));
+        FL_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), st));
+        TcArgs a{};
+        a.n = rows;
+        a.P = P;
+        a.d = d;
+        a.L = L;
+        a.K = K;
+        a.xnorm = xn;
+        a.wnorm = ix->w_norm;
+        a.c_norm = c_norm;
+        a.tiny = tiny;
+        a.codes = buckets + r0 * L;
+        a.proj = proj ? proj + r0 * P : nullptr;
+        a.rlist = list1;
+        a.rcount = cnt;
+        a.err = ix->tc_err;
+        dim3 grid((unsigned)((rows + kTM - 1) / kTM), (P + kTN - 1) / kTN);
+        k_srp_tc<<<grid, 192, smem, st>>>(mx1, mx2, mw1, mw2, a);
+        count_launch();
+        FL_CUDA(cudaGetLastError());
+        // stage 2: compensated fp32; stage 3: fp64 / exact
+        k_srp_recheck2<<<152 * 4, 256, 0, st>>>(x + r0 * ld, ld, ix->srp_w, d, L, K, g2, tiny, list1, cnt,
+                                               buckets + r0 * L, list2, cnt + 1, ix->stats + 3);
+        count_launch();
+        FL_CUDA(cudaGetLastError());
+        FL_TRY(srp_recheck_list(ix, x + r0 * ld, ld, list2, cnt + 1, buckets + r0 * L));
+        FL_TRY(add_counter(ix->stats, cnt, st));            // undecided after the tensor-core pass
+    }
+    FL_CUDA(cudaMemcpyAsync(ix->h_flag, ix->tc_err, 4, cudaMemcpyDeviceToHost, st));
+    FL_CUDA(cudaStreamSynchronize(st));
+    if (*ix->h_flag) return set_error(FLINNG_ERR_TIMEOUT, "tensor-core SRP: a pipeline wait timed out");
+    return FLINNG_OK;
+}
+
+}  // namespace flinng

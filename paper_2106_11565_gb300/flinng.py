@@ -19,7 +19,7 @@ from . import _build
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT = range(6)
 COSINE_SRP, JACCARD_DOPH = 0, 1
-PREC_FP32 = 0
+PREC_FP32, PREC_BF16X2 = 0, 1
 QUERY_PLAIN, QUERY_FUSED, QUERY_GRAPH = 0, 1, 2
 
 
@@ -184,7 +184,8 @@ class Index:
     """
 
     def __init__(self, metric: str, R: int, B: int, L: int, K: int, capacity: int,
-                 params, dim: int = 0, W: int | None = None, t_min: int = 1, stream=None):
+                 params, dim: int = 0, W: int | None = None, t_min: int = 1, stream=None,
+                 precision: int = PREC_FP32):
         self.lib = load()
         self.metric = metric
         self.cfg = flinng_config()
@@ -193,7 +194,7 @@ class Index:
         self.cfg.R, self.cfg.B, self.cfg.L, self.cfg.K = R, B, L, K
         self.cfg.range_bits = K if W is None else W
         self.cfg.min_threshold = t_min
-        self.cfg.precision = PREC_FP32
+        self.cfg.precision = precision
         self.cfg.capacity = capacity
         self.R, self.B, self.L, self.K, self.W = R, B, L, K, self.cfg.range_bits
         p = flinng_params()
