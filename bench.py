@@ -56,7 +56,7 @@ WORKLOADS = {
                chunk=32768,
                desc="cosine/SRP YFCC-shaped embeddings N=10000000 d=4096 (ReLU of a 1000-centre "
                     "Gaussian mixture, streamed from a seed on the GPU, never stored) R3 B20000 L64 K16 "
-                    "FP32 nq=10000 k=10"),
+                    "nq=10000 k=10"),
     "C3": dict(metric="jaccard", url=True, N=1_000_000, nq=10_000, R=4, B=5000, L=64, K=1, W=17,
                k=10, gt_sample=500,
                desc="Jaccard/DOPH URL-shaped strings N=1000000 (lognormal length, median 60, Zipf(1.1) "
@@ -503,8 +503,10 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
         import torch.distributed as dist
     nq, k, L = c["nq"], c["k"], c["L"]
 
+    prec = F.PREC_BF16X2 if (args.precision == "bf16x2" and c["metric"] == "cosine") else F.PREC_FP32
+    prec_name = {F.PREC_FP32: "FP32 FFMA", F.PREC_BF16X2: "BF16x2 tcgen05"}[prec]
     ix = F.Index(c["metric"], c["R"], c["B"], L, c["K"], capacity=c["N"], params=c["params"],
-                 dim=c.get("d", 0), W=c["W"])
+                 dim=c.get("d", 0), W=c["W"], precision=prec)
 
     def to_dev_points(p):
         if c["metric"] == "cosine":
@@ -525,8 +527,8 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
         def build_once():
             build_streamed(F, ix, c, dev, d_perm)
         n_builds, n_warm = 1, 0
-        build_note = ("streamed: generate 32768-point chunks on the device, FP32 SRP GEMM, keep buckets; "
-                      "then flinng_build_buckets (generation included)")
+        build_note = (f"streamed: generate 32768-point chunks on the device, {prec_name} SRP GEMM, keep "
+                      "buckets; then flinng_build_buckets (generation included)")
     else:
         d_pts = to_dev_points(c["pts"])
         d_q = to_dev_points(c["q"])
@@ -631,6 +633,7 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     torch.cuda.synchronize()
     t_end2 = time.time()
     clk = clocks.stop(t_load, max(t_end, t_end2))
+    hcnt = ix.hash_counters() if c["metric"] == "cosine" else None     # the last plain-form hash
     hash_ms = [a.elapsed_time(m) for a, m, _ in pev]
     query_ms = [m.elapsed_time(b) for _, m, b in pev]
     plain_ms = [a.elapsed_time(b) for a, _, b in pev]
@@ -721,7 +724,18 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     h_mean = statistics.mean(hash_ms)
     big_srp = c["metric"] == "cosine" and c["L"] * c["K"] * c["d"] > (1 << 18)
     sm_max = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0)
-    if big_srp and h_mean > q_mean:
+    if big_srp and h_mean > q_mean and prec == F.PREC_BF16X2:
+        # the dominant stage is the tensor-core SRP (split, tcgen05 GEMM, re-checks)
+        flops = 2.0 * nq * c["d"] * c["L"] * c["K"]
+        achieved = flops / (h_mean / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops", 1900.0)
+        roof = {"kernel": "k_srp_tc (+ k_split_rows, re-checks)", "bound": "tensor", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "algorithmic_flops_per_launch": flops,
+                "issued_tensor_flops_per_launch": 3 * flops,
+                "peak_source": ("measured" if "bf16_tflops" in peaks else "fallback") + " bf16_tflops (burst)",
+                "note": "algorithmic FLOPs = 2 n d L K; the two-term split issues three BF16 MMAs per product"}
+    elif big_srp and h_mean > q_mean:
         # the timed step's dominant kernel is the FP32 SRP GEMM: FMA-pipe bound
         dom = "k_srp_fp32 (+ k_srp_recheck)"
         flops = 2.0 * nq * c["d"] * c["L"] * c["K"]
@@ -756,6 +770,7 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
         "scaling": "weak", "vs_baseline": None, "dtype": "u32" if c["metric"] != "cosine" else "f32",
         "data": "synthetic (seeded; stands in for the paper's datasets)",
         "config": {"workload": f"{args.workload}: {c['desc']}",
+                   "srp_precision": prec_name if c["metric"] == "cosine" else None,
                    "form": "fused: one persistent kernel per batch (hash, gather, decode, top-k), "
                            "CUDA graph per batch-size class, autotuned launch shape",
                    "tuning": tuning,
@@ -769,8 +784,15 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
                        "stages_ms": {"hash": h_mean, "count_decode_topk": q_mean},
                        "kernels": "k_doph|k_srp_fp32+k_srp_recheck, then k_query"},
         "build": {"ms": statistics.mean(build_ms), "points_per_s": c["N"] / (statistics.mean(build_ms) / 1e3),
+                  "hash_precision": prec_name if c["metric"] == "cosine" else None,
                   "n_cells": int(ex["off"][-1]), "how": build_note},
         "roofline": roof,
+        "hash_counters": None if hcnt is None else dict(
+            hcnt, precision=prec_name, projections=nq * c["L"] * c["K"],
+            first_pass_undecided_rate=hcnt["undecided"] / (nq * c["L"] * c["K"]),
+            flip_rate_before_recheck=hcnt["flips"] / (nq * c["L"] * c["K"]),
+            note="last plain-form hash of the query batch; undecided projections are re-checked "
+                 "(compensated fp32, fp64, exact), so the codes stay exact"),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "api": "flinng_query, host pinned buffers"},
         "gpu_launches": int(launches),
@@ -972,6 +994,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-form traces")
     ap.add_argument("--no-recall", action="store_true", help="skip the exact ground truth (profiling runs)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x2"],
+                    help="SRP projection arithmetic for cosine workloads (signs are exact either way)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

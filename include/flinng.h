@@ -250,6 +250,15 @@ int flinng_export(flinng_index *idx, uint32_t *off, uint16_t *cells,
 int flinng_hash_stats(const flinng_index *idx, uint64_t *n_recheck,
                       uint64_t *n_exact);
 
+/* All counters of the last cosine hash, or query (Sec. 3.2 signs), on this
+ * index: out[0] projections the first pass (fp32 FMA or tensor cores) could
+ * not decide; out[1] those decided by the exact accumulator; out[2] fp64
+ * re-checks; out[3] compensated fp32 re-checks (tensor-core precision only);
+ * out[4] flips: first-pass signs that a re-check reversed (the hash-bit flip
+ * rate before re-check is out[4] / (n * L * K)). out: 5 HOST uint64, written
+ * after the index's stream is synchronised. Errors: INVALID_ARG for NULL. */
+int flinng_hash_counters(const flinng_index *idx, uint64_t *out);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * indices, all threads); memset/memcpy operations are not counted. */
 uint64_t flinng_kernel_launches(void);

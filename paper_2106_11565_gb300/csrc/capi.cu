@@ -654,4 +654,14 @@ int flinng_hash_stats(const flinng_index *idx, uint64_t *n_recheck, uint64_t *n_
     return FLINNG_OK;
 }
 
+int flinng_hash_counters(const flinng_index *idx, uint64_t *out)
+{
+    if (!idx || !out) return set_error(FLINNG_ERR_INVALID_ARG, "hash_counters: null argument");
+    unsigned long long h[kStats] = {};
+    FL_CUDA(cudaStreamSynchronize(idx->stream));
+    FL_CUDA(cudaMemcpy(h, idx->stats, sizeof h, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < kStats; ++i) out[i] = h[i];
+    return FLINNG_OK;
+}
+
 }  // extern "C"

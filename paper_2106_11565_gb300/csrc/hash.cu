@@ -85,7 +85,7 @@ k_srp_fp32(const float *__restrict__ X, uint64_t ldx, uint64_t n,
                 if (p[i][j] > 0.f) atomicOr(&codes[gr * L + gc / K], 1u << (gc % K));
             } else {
                 const unsigned long long slot = atomicAdd(rcount, 1ull);
-                rlist[slot] = ((unsigned long long)gr << 20) | gc;
+                rlist[slot] = (p[i][j] > 0.f ? kEntSign : 0ull) | ((unsigned long long)gr << 20) | gc;
             }
         }
     }
@@ -148,8 +148,8 @@ __global__ void k_srp_recheck(const float *__restrict__ X, uint64_t ldx,
     for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
          e < nlist; e += nwarps) {
         const unsigned long long ent = rlist[e];
-        const uint64_t gr = ent >> 20;
-        const uint32_t gc = uint32_t(ent & 0xFFFFF);
+        const uint64_t gr = ent_row(ent);
+        const uint32_t gc = ent_col(ent);
         const float *xr = X + gr * ldx;
         const float *wr = Wm + uint64_t(gc) * d;
         double p = 0.0, s = 0.0;
@@ -186,6 +186,7 @@ __global__ void k_srp_recheck(const float *__restrict__ X, uint64_t ldx,
         if (lane == 0) {
             if (positive) atomicOr(&codes[gr * L + gc / K], 1u << (gc % K));
             atomicAdd(&stats[2], 1ull);
+            if (positive != ((ent & kEntSign) != 0)) atomicAdd(&stats[4], 1ull);
         }
     }
 }

@@ -14,8 +14,14 @@ constexpr uint64_t kKeyNone = ~0ull;
 constexpr uint32_t kMaxKMax = 1024;
 constexpr uint32_t kDophMaxAttempts = 4096;
 // hash counters: [0] undecided after the first pass, [1] exact accumulator,
-// [2] fp64 re-checks, [3] compensated fp32 re-checks
-constexpr int kStats = 4;
+// [2] fp64 re-checks, [3] compensated fp32 re-checks, [4] first-pass signs
+// that a re-check reversed (flips)
+constexpr int kStats = 5;
+// re-check list entries: bit 63 the first pass's tentative sign (p > 0),
+// bits 20..62 the row, bits 0..19 the projection
+constexpr unsigned long long kEntSign = 1ull << 63;
+__host__ __device__ inline uint64_t ent_row(unsigned long long e) { return (e >> 20) & ((1ull << 43) - 1); }
+__host__ __device__ inline uint32_t ent_col(unsigned long long e) { return uint32_t(e & 0xFFFFF); }
 
 // Error plumbing: every internal step returns an int status and leaves a
 // message in the thread-local buffer.

@@ -705,6 +705,7 @@ __device__ void cta_srp(const QArgs &a, const HArgs &h, uint32_t q, uint32_t *qb
             if (lane == 0) {
                 atomicAdd(&h.stats[0], 1ull);
                 atomicAdd(&h.stats[2], 1ull);
+                if (positive != (p > 0.f)) atomicAdd(&h.stats[4], 1ull);
             }
         }
         if (lane == 0 && positive) atomicOr(&qb[j / h.K], 1u << (j % h.K));

@@ -2,27 +2,36 @@
 // dense contraction P = X W^T runs on tcgen05 with BF16 operands and FP32
 // accumulation in tensor memory, and the sign bits stay exact.
 //
-// Exactness. Each fp32 operand is split exactly enough: x1 = bf16(x),
-// x2 = bf16(x - x1), so |x - x1 - x2| <= 2^-16 |x| (bf16 keeps 8 significant
-// bits); likewise w. bf16 x bf16 products are exact in fp32. The tile
-// computes hi = sum x1 w1 and lo = sum (x1 w2 + x2 w1) in two TMEM
-// accumulators; p~ = hi + lo differs from the exact w.x by at most
-//   (g(d) + 2^-7 g(2d) + 3.1 * 2^-16) (1 + 2^-8)^2 ||x|| ||w|| + 2^-23 |p~| + d 2^-130
-// with g(n) = n u' / (1 - n u'), u' = 2^-22: four units of fp32 rounding per
-// accumulation step, which also covers a truncating tensor-core adder.
-// Projections whose |p~| does not clear that margin go to a compensated fp32
-// re-check (two-product, two-sum), and the few that stay ambiguous to the
-// fp64 / exact re-check of hash.cu.
+// Exactness. Each fp32 operand is split as x1 = bf16(x), x2 = bf16(x - x1),
+// so |x - x1 - x2| <= 2^-16 |x| (bf16 keeps 8 significant bits); likewise w.
+// bf16 x bf16 products are exact in fp32. Per 64-wide k-block s the tensor
+// cores compute hi_s = sum x1 w1 and lo_s = sum (x1 w2 + x2 w1) into a fresh
+// pair of TMEM accumulators; the epilogue adds hi_s + lo_s into an fp32
+// register per projection. Short accumulation chains keep the bound tight:
+//   |p~ - w.x| <= [g'(64) + 2^-7 g'(128)] (1 + 2^-8)^2 ||x|| ||w||      (blocks)
+//              + g(2m) (1 + g'(64)) (1 + 2^-7) (1 + 2^-8)^2 ||x|| ||w||  (sum of m blocks)
+//              + 3.1 * 2^-16 ||x|| ||w||                                 (split)
+//              + 8 d 2^-126 + sqrt(d) 2^-125 (||x|| + ||w||)           (underflow, flushes)
+// with g(n) = n u / (1 - n u), u = 2^-24, and g' the same with u' = 2^-22:
+// four units of fp32 rounding per product accumulated, which also covers a
+// tensor-core adder that aligns and truncates. Projections whose |p~| does
+// not clear that margin go to a compensated fp32 re-check (two-product,
+// two-sum), and the few that stay ambiguous to the fp64 / exact re-check of
+// hash.cu.
 //
-// Kernel layout (one CTA per 128 points x 128 projections, 192 threads):
+// Kernel layout (one CTA per 128 points x 128 projections, 320 threads):
 //   warp 0     TMA producer: 3-stage ring of {X1, X2, W1, W2} tiles of 128 rows
 //              x 64 bf16 (128-byte swizzle), one mbarrier per stage;
-//   warp 1     allocates 256 TMEM columns, one elected thread issues the MMAs
-//              (M=128, N=128, K=16) and commits each stage back to the producer;
-//   warps 2-5  epilogue: each reads its 32 TMEM lanes (one point per thread),
-//              decides the signs, writes the codes, lists ambiguous projections.
+//   warp 1     allocates 512 TMEM columns (two buffers of {hi, lo}); one elected
+//              thread issues the MMAs (M=128, N=128, K=16) of k-block s into
+//              buffer s % 2, then commits the stage back to the producer and the
+//              buffer to the epilogue;
+//   warps 2-9  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +32 (one point per
+//              thread) and 64 of the 128 columns, drains each buffer into fp32
+//              registers and hands it back; at the end decides the signs,
+//              writes the codes and lists ambiguous projections.
 // Every wait on an mbarrier is bounded; on timeout the CTA sets an error flag,
-// stops issuing work, waits (bounded) for the copies it issued and frees TMEM.
+// stops issuing work, waits (bounded) for its copies and MMAs, and frees TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -35,7 +44,9 @@ constexpr int kTM = 128, kTN = 128, kTK = 64;     // tile rows, projections, K p
 constexpr int kStages = 3;
 constexpr int kTileBytes = kTM * kTK * 2;         // 16 KB per operand tile
 constexpr int kStageBytes = 4 * kTileBytes;       // X1, X2, W1, W2
-constexpr uint32_t kTmemCols = 256;               // hi: cols [0,128), lo: [128,256)
+constexpr uint32_t kTmemCols = 512;               // buffer b: hi at 256 b, lo at 256 b + 128
+constexpr int kEpiWarps = 8;                      // two per TMEM lane quarter, 64 columns each
+constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 constexpr uint64_t kWaitNs = 1000000000ull;       // bounded mbarrier waits: 1 s
 constexpr uint64_t kTcChunkRows = 16384;          // rows split and hashed per launch
 
@@ -150,7 +161,8 @@ struct TcArgs {
     const float *xnorm;    // n: upper bounds of ||x||
     const float *wnorm;    // P: upper bounds of ||w||
     float c_norm;          // margin factor on ||x|| ||w||
-    float tiny;
+    float c_sub;           // margin factor on ||x|| + ||w|| (subnormal flushes)
+    float tiny;            // absolute margin (underflow)
     uint32_t *codes;       // n x L (zeroed)
     float *proj;           // optional n x P
     unsigned long long *rlist;
@@ -158,7 +170,12 @@ struct TcArgs {
     uint32_t *err;         // set to 1 on a wait timeout
 };
 
-__global__ void __launch_bounds__(192, 1)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
 k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtensorMap mx2,
          const __grid_constant__ CUtensorMap mw1, const __grid_constant__ CUtensorMap mw2, TcArgs a)
 {
@@ -166,9 +183,11 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
     // 1024-byte aligned tile ring, then barriers and the TMEM address
     unsigned char *ring = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
     uint64_t *full = reinterpret_cast<uint64_t *>(ring + kStages * kStageBytes);
-    uint64_t *empty = full + kStages;
-    uint64_t *accd = empty + kStages;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accd + 1);
+    uint64_t *empty = full + kStages;        // stage consumed by the MMAs
+    uint64_t *tfull = empty + kStages;       // TMEM buffer b holds a finished k-block
+    uint64_t *tempty = tfull + 2;            // TMEM buffer b drained by the epilogue
+    uint64_t *mdone = tempty + 2;            // every MMA issued has completed
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 1);
     uint32_t *abort_flag = tmem_slot + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -180,7 +199,11 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accd, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kEpiWarps);
+        }
+        mbar_init(mdone, 1);
         *abort_flag = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -217,15 +240,18 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t t_hi = tmem, t_lo = tmem + kTN;
             for (uint32_t kb = 0; kb < nkb; ++kb) {
                 const int s = kb % kStages;
-                if (!mbar_wait(&full[s], (kb / kStages) & 1)) {
+                const uint32_t b = kb & 1u;
+                if (!mbar_wait(&full[s], (kb / kStages) & 1) ||
+                    (kb >= 2 && !mbar_wait(&tempty[b], ((kb >> 1) - 1) & 1))) {
                     atomicExch(abort_flag, 1u);
                     break;
                 }
+                if (*(volatile uint32_t *)abort_flag) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t st = smem_u32(ring + s * kStageBytes);
+                const uint32_t t_hi = tmem + 256u * b, t_lo = t_hi + kTN;
 #pragma unroll
                 for (int kk = 0; kk < kTK / 16; ++kk) {
                     const uint32_t off = kk * 32;
@@ -233,42 +259,64 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
                     const uint64_t x2 = smem_desc(st + 1 * kTileBytes + off);
                     const uint64_t w1 = smem_desc(st + 2 * kTileBytes + off);
                     const uint64_t w2 = smem_desc(st + 3 * kTileBytes + off);
-                    const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                    const uint32_t acc = kk > 0 ? 1u : 0u;     // each k-block starts a fresh pair
                     mma_bf16(t_hi, x1, w1, acc);
                     mma_bf16(t_lo, x1, w2, acc);
                     mma_bf16(t_lo, x2, w1, 1u);
                 }
                 mma_commit(&empty[s]);
+                mma_commit(&tfull[b]);
             }
-            mma_commit(accd);      // arrives once every MMA issued above has completed
+            mma_commit(mdone);     // arrives once every MMA issued above has completed
         }
     } else {
-        // epilogue: warp w reads TMEM lanes [32 (w % 4), +32): one point per thread
+        // epilogue: TMEM lanes [32 (warp % 4), +32) = one point per thread;
+        // columns [64 half, +64) of the tile
         const uint32_t quarter = (warp & 3) * 32;
-        uint32_t got = 0;
-        if (lane == 0) got = mbar_wait(accd, 0) ? 1u : 0u;
-        got = __shfl_sync(0xffffffffu, got, 0);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!got && lane == 0) atomicExch(abort_flag, 1u);
+        const uint32_t half = uint32_t(warp - 2) >> 2;
+        const uint32_t tbase = tmem + (quarter << 16) + 64u * half;
+        float acc[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+        bool abort = false;
+        for (uint32_t kb = 0; kb < nkb; ++kb) {
+            const uint32_t b = kb & 1u;
+            uint32_t got = 0;
+            if (lane == 0) got = mbar_wait(&tfull[b], (kb >> 1) & 1) ? 1u : 0u;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) {
+                if (lane == 0) atomicExch(abort_flag, 1u);
+                abort = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                float hi[16], lo[16];
+                tmem_ld16(tbase + 256u * b + c0, hi);
+                tmem_ld16(tbase + 256u * b + kTN + c0, lo);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[c0 + j] += hi[j] + lo[j];
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
         uint32_t ab = lane == 0 ? *(volatile uint32_t *)abort_flag : 0u;
-        const bool abort = __shfl_sync(0xffffffffu, ab, 0) != 0u;   // warp-uniform
+        abort = abort || __shfl_sync(0xffffffffu, ab, 0) != 0u;    // warp-uniform
         const uint64_t row = uint64_t(row0) + quarter + lane;
-        const bool row_ok = row < a.n && !abort;
-        const float xn = row_ok ? a.xnorm[row] : 0.f;
-        for (uint32_t c0 = 0; c0 < uint32_t(kTN) && !abort; c0 += 16) {
-            float hi[16], lo[16];
-            __syncwarp();          // the TMEM loads below are warp-collective
-            tmem_ld16(tmem + (quarter << 16) + c0, hi);
-            tmem_ld16(tmem + (quarter << 16) + kTN + c0, lo);
-            if (!row_ok) continue;
+        if (!abort && row < a.n) {
+            const float xn = a.xnorm[row];
             uint32_t cur_l = 0xFFFFFFFFu, cur_bits = 0u;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const uint32_t col = col0 + c0 + j;
-                if (col >= a.P) continue;
-                const float p = hi[j] + lo[j];
+            for (int j = 0; j < 64; ++j) {
+                const uint32_t col = col0 + 64u * half + j;
+                if (col >= a.P) break;
+                const float p = acc[j];
+                const float wn = a.wnorm[col];
                 if (a.proj) a.proj[row * a.P + col] = p;
-                const float margin = fmaf(a.c_norm * xn, a.wnorm[col], fmaf(ldexpf(1.f, -23), fabsf(p), a.tiny));
+                const float margin =
+                    fmaf(a.c_norm * xn, wn, fmaf(ldexpf(1.f, -23), fabsf(p), fmaf(a.c_sub, xn + wn, a.tiny)));
                 if (fabsf(p) > margin) {
                     if (p > 0.f) {
                         const uint32_t l = col / a.K;
@@ -281,7 +329,7 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
                     }
                 } else {
                     const unsigned long long slot = atomicAdd(a.rcount, 1ull);
-                    a.rlist[slot] = ((unsigned long long)row << 20) | col;
+                    a.rlist[slot] = (p > 0.f ? kEntSign : 0ull) | ((unsigned long long)row << 20) | col;
                 }
             }
             if (cur_bits) atomicOr(&a.codes[row * a.L + cur_l], cur_bits);
@@ -296,12 +344,15 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
             for (uint32_t kb = (issued > uint32_t(kStages) ? issued - kStages : 0); kb < issued; ++kb)
                 mbar_wait(&full[kb % kStages], (kb / kStages) & 1);
         }
-        __syncthreads();
     }
     if (warp == 1) {
+        // every MMA has completed before the columns are freed
+        if (lane == 0) mbar_wait(mdone, 0);
+        __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }
+    __syncthreads();
 }
 
 // x -> (bf16(x), bf16(x - bf16(x))) and an upper bound of each row's norm
@@ -337,7 +388,7 @@ __global__ void k_srp_recheck2(const float *__restrict__ X, uint64_t ldx, const 
                                const unsigned long long *__restrict__ rlist,
                                const unsigned long long *__restrict__ rcount, uint32_t *__restrict__ codes,
                                unsigned long long *__restrict__ out_list, unsigned long long *__restrict__ out_count,
-                               unsigned long long *__restrict__ stats)   // stats: compensated re-check counter
+                               unsigned long long *__restrict__ stats)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long nlist = *rcount;
@@ -345,8 +396,8 @@ __global__ void k_srp_recheck2(const float *__restrict__ X, uint64_t ldx, const 
     for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
          e < nlist; e += nwarps) {
         const unsigned long long ent = rlist[e];
-        const uint64_t gr = ent >> 20;
-        const uint32_t gc = uint32_t(ent & 0xFFFFF);
+        const uint64_t gr = ent_row(ent);
+        const uint32_t gc = ent_col(ent);
         const float *xr = X + gr * ldx;
         const float *wr = Wm + uint64_t(gc) * d;
         float s = 0.f, c = 0.f, sa = 0.f;
@@ -378,10 +429,11 @@ __global__ void k_srp_recheck2(const float *__restrict__ X, uint64_t ldx, const 
         if (lane == 0) {
             if (fabsf(p) > margin) {
                 if (p > 0.f) atomicOr(&codes[gr * L + gc / K], 1u << (gc % K));
+                if ((p > 0.f) != ((ent & kEntSign) != 0)) atomicAdd(&stats[4], 1ull);
             } else {
                 out_list[atomicAdd(out_count, 1ull)] = ent;
             }
-            atomicAdd(stats, 1ull);
+            atomicAdd(&stats[3], 1ull);
         }
     }
 }
@@ -473,13 +525,17 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
     CUtensorMap mw1, mw2;
     FL_TRY(make_map(&mw1, w1, P, d));
     FL_TRY(make_map(&mw2, w1 + size_t(P) * d, P, d));
-    // margin factor (see the header comment), in double then rounded up
-    const double up = std::ldexp(1.0, -22);
-    auto g = [&](double m) { return m * up / (1.0 - m * up); };
-    const double f = (g(d) + std::ldexp(1.0, -7) * g(2.0 * d) + 3.1 * std::ldexp(1.0, -16)) *
-                     (1 + std::ldexp(1.0, -8)) * (1 + std::ldexp(1.0, -8));
+    // margin factors (see the header comment), in double then rounded up
+    const double u = std::ldexp(1.0, -24), up = std::ldexp(1.0, -22);
+    auto g = [](double m, double uu) { return m * uu / (1.0 - m * uu); };
+    const double q = (1 + std::ldexp(1.0, -8)) * (1 + std::ldexp(1.0, -8));
+    const double m_blocks = double((d + kTK - 1) / kTK);
+    const double f = (g(kTK, up) + std::ldexp(1.0, -7) * g(2 * kTK, up)) * q +
+                     g(2 * m_blocks, u) * (1 + g(kTK, up)) * (1 + std::ldexp(1.0, -7)) * q +
+                     3.1 * std::ldexp(1.0, -16);
     const float c_norm = std::nextafter(float(f * 1.0001), INFINITY);
-    const float tiny = float(d) * std::ldexp(1.0f, -126);
+    const float c_sub = std::nextafter(float(std::sqrt(double(d)) * std::ldexp(1.0, -125)), INFINITY);
+    const float tiny = std::nextafter(float(8.0 * d * std::ldexp(1.0, -126)), INFINITY);
     const double g2d = 2.0 * d * std::ldexp(1.0, -24) / (1.0 - 2.0 * d * std::ldexp(1.0, -24));
     const float g2 = std::nextafter(float(2.0 * g2d * g2d + std::ldexp(1.0, -40)), INFINITY);
     const size_t smem = size_t(kStages) * kStageBytes + 1024 + 256;
@@ -502,6 +558,7 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
         a.xnorm = xn;
         a.wnorm = ix->w_norm;
         a.c_norm = c_norm;
+        a.c_sub = c_sub;
         a.tiny = tiny;
         a.codes = buckets + r0 * L;
         a.proj = proj ? proj + r0 * P : nullptr;
@@ -509,12 +566,12 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
         a.rcount = cnt;
         a.err = ix->tc_err;
         dim3 grid((unsigned)((rows + kTM - 1) / kTM), (P + kTN - 1) / kTN);
-        k_srp_tc<<<grid, 192, smem, st>>>(mx1, mx2, mw1, mw2, a);
+        k_srp_tc<<<grid, kTcThreads, smem, st>>>(mx1, mx2, mw1, mw2, a);
         count_launch();
         FL_CUDA(cudaGetLastError());
         // stage 2: compensated fp32; stage 3: fp64 / exact
         k_srp_recheck2<<<152 * 4, 256, 0, st>>>(x + r0 * ld, ld, ix->srp_w, d, L, K, g2, tiny, list1, cnt,
-                                               buckets + r0 * L, list2, cnt + 1, ix->stats + 3);
+                                               buckets + r0 * L, list2, cnt + 1, ix->stats);
         count_launch();
         FL_CUDA(cudaGetLastError());
         FL_TRY(srp_recheck_list(ix, x + r0 * ld, ld, list2, cnt + 1, buckets + r0 * L));

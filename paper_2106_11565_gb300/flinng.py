@@ -93,6 +93,7 @@ _SIGS = {
     "flinng_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64,
                                 C.POINTER(C.c_uint64), C.c_void_p]),
     "flinng_hash_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    "flinng_hash_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     "flinng_kernel_launches": (C.c_uint64, []),
     "flinng_set_query_mode": (C.c_int, [C.c_void_p, C.c_uint32]),
     "flinng_tune_query": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint32, C.c_uint32,
@@ -339,6 +340,13 @@ class Index:
         a, b = C.c_uint64(), C.c_uint64()
         _check(self.lib.flinng_hash_stats(self.h, C.byref(a), C.byref(b)))
         return int(a.value), int(b.value)
+
+    def hash_counters(self) -> dict:
+        """Counters of the last cosine hash or query: undecided after the
+        first pass, exact, fp64 and compensated re-checks, sign flips."""
+        out = (C.c_uint64 * 5)()
+        _check(self.lib.flinng_hash_counters(self.h, out))
+        return dict(zip(("undecided", "exact", "fp64", "compensated", "flips"), (int(v) for v in out)))
 
 
 def generate_embeddings(seed: int, dim: int, n_centers: int, sigma: float, first: int, n: int,
