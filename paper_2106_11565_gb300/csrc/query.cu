@@ -30,7 +30,8 @@ namespace flinng {
 
 namespace {
 
-constexpr int kQTmax = 256;              // CTA size of the plain and counts kernels
+constexpr int kQTmax = 256;              // CTA size of the counts kernel
+constexpr int kPlainUnroll = 4;          // plain kernel: loads in flight per thread
 constexpr uint64_t kKeyBits = (1ull << 56) - 1;
 
 struct QArgs {
@@ -298,7 +299,7 @@ __device__ uint64_t block_compact(const QSmem &s, uint32_t nbuf, uint32_t kk)
 // and adds 4 bits at a time (spread to the 4 bytes of the word) without
 // atomics. The other tables' lists are flattened over the CTA and counted
 // with shared-memory atomics. Contains __syncthreads.
-template <int NT>
+template <int NT, int U = 1>
 __device__ void gather_counts(const QArgs &a, const QSmem &s, const uint32_t *qb)
 {
     const int tid = threadIdx.x;
@@ -344,10 +345,21 @@ __device__ void gather_counts(const QArgs &a, const QSmem &s, const uint32_t *qb
         s.c_pre[tid] = pre;
         __syncthreads();
         const uint32_t nl = min(uint32_t(NT), a.L - l0);
-        for (uint32_t e = tid; e < total; e += NT) {
-            const uint32_t t = find_seg(s.c_pre, nl, e);
-            const uint32_t c = a.cells[s.c_start[t] + (e - s.c_pre[t])];
-            atomicAdd(&s.cntw[c >> 2], 1u << ((c & 3) * 8));
+        // U cell loads in flight per thread before their counter updates
+        for (uint32_t e0 = tid; e0 < total; e0 += NT * U) {
+            uint32_t c[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t e = e0 + uint32_t(u) * NT;
+                c[u] = kEmpty32;
+                if (e < total) {
+                    const uint32_t t = find_seg(s.c_pre, nl, e);
+                    c[u] = a.cells[s.c_start[t] + (e - s.c_pre[t])];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (c[u] != kEmpty32) atomicAdd(&s.cntw[c[u] >> 2], 1u << ((c[u] & 3) * 8));
         }
         __syncthreads();
     }
@@ -368,7 +380,7 @@ __device__ inline void zero_query_state(const QArgs &a, const QSmem &s)
 
 // Group tests, AND-over-R decode and top-k of query q, from the counts in
 // shared memory; writes row q of the outputs.
-template <int NT, int RW>
+template <int NT, int RW, int U = 1>
 __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t kq)
 {
     uint16_t *lvl_cells = lvl_cells_ptr(s, a.BR);
@@ -419,46 +431,61 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                 for (uint32_t j0 = 0; j0 < M; j0 += sub) {
                     const uint32_t jn = min(M, j0 + sub);
                     if (s.u[0] + (jn - j0) > a.cap) bound = block_compact<NT>(s, s.u[0], kq);
-                    // warp-uniform trip count: every lane of a warp runs every iteration
-                    for (uint32_t jb = j0 + (tid & ~31u); jb < jn; jb += NT) {
-                        const uint32_t j = jb + lane;
-                        bool valid = false;
-                        uint32_t score = 256, last = 0, x = 0;
-                        if (j < jn) {
-                            const uint32_t cs = find_seg(s.c_pre, ncc, j);
-                            uint32_t w[RW];
-                            load_record<RW>(a.mrec, s.c_start[cs] + (j - s.c_pre[cs]), w);
-                            x = w[0];
-                            // repetition 0: the cell itself, at count t
-                            score = uint32_t(t);
-                            last = s.c_cell[cs];
+                    // warp-uniform trip count: every lane of a warp runs every
+                    // iteration; U member records per lane are loaded before
+                    // any is decoded, so U loads are in flight per thread
+                    for (uint32_t jb = j0 + (tid & ~31u); jb < jn; jb += NT * U) {
+                        uint32_t w[U][RW];
+                        uint32_t cell[U];
+                        bool in[U];
 #pragma unroll
-                            for (int r = 1; r < 2 * RW - 1; ++r) {
-                                if (r < int(a.R)) {
-                                    const uint32_t g = (w[1 + (r - 1) / 2] >> (16 * ((r - 1) & 1))) & 0xFFFFu;
-                                    const uint32_t c = uint32_t(r) * a.B + g;
-                                    const uint32_t v = cnt8[c];
-                                    if (v < score) {
-                                        score = v;
-                                        last = c;
-                                    } else if (v == score) {
-                                        last = c;
+                        for (int u = 0; u < U; ++u) {
+                            const uint32_t j = jb + uint32_t(u) * NT + lane;
+                            in[u] = j < jn;
+                            cell[u] = 0;
+                            if (in[u]) {
+                                const uint32_t cs = find_seg(s.c_pre, ncc, j);
+                                cell[u] = s.c_cell[cs];
+                                load_record<RW>(a.mrec, s.c_start[cs] + (j - s.c_pre[cs]), w[u]);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            bool valid = false;
+                            uint32_t score = 256, last = 0, x = 0;
+                            if (in[u]) {
+                                x = w[u][0];
+                                // repetition 0: the cell itself, at count t
+                                score = uint32_t(t);
+                                last = cell[u];
+#pragma unroll
+                                for (int r = 1; r < 2 * RW - 1; ++r) {
+                                    if (r < int(a.R)) {
+                                        const uint32_t g = (w[u][1 + (r - 1) / 2] >> (16 * ((r - 1) & 1))) & 0xFFFFu;
+                                        const uint32_t c = uint32_t(r) * a.B + g;
+                                        const uint32_t v = cnt8[c];
+                                        if (v < score) {
+                                            score = v;
+                                            last = c;
+                                        } else if (v == score) {
+                                            last = c;
+                                        }
                                     }
                                 }
+                                valid = score >= a.t_min;
                             }
-                            valid = score >= a.t_min;
-                        }
-                        // points seen per score: one shared-memory atomic per distinct score per warp
-                        const uint32_t grp = __match_any_sync(0xffffffffu, valid ? score : 0xFFFFu);
-                        if (valid && lane == __ffs(grp) - 1) atomicAdd(&s.hist_s[score], __popc(grp));
-                        const uint64_t key = (uint64_t(255u - score) << 48) | (uint64_t(last) << 32) | x;
-                        const bool want = valid && key <= bound;
-                        const uint32_t wm = __ballot_sync(0xffffffffu, want);
-                        if (wm) {
-                            uint32_t base = 0;
-                            if (lane == __ffs(wm) - 1) base = atomicAdd(&s.u[0], __popc(wm));
-                            base = __shfl_sync(0xffffffffu, base, __ffs(wm) - 1);
-                            if (want) s.buf[base + __popc(wm & ((1u << lane) - 1u))] = key;
+                            // points seen per score: one shared-memory atomic per distinct score per warp
+                            const uint32_t grp = __match_any_sync(0xffffffffu, valid ? score : 0xFFFFu);
+                            if (valid && lane == __ffs(grp) - 1) atomicAdd(&s.hist_s[score], __popc(grp));
+                            const uint64_t key = (uint64_t(255u - score) << 48) | (uint64_t(last) << 32) | x;
+                            const bool want = valid && key <= bound;
+                            const uint32_t wm = __ballot_sync(0xffffffffu, want);
+                            if (wm) {
+                                uint32_t base = 0;
+                                if (lane == __ffs(wm) - 1) base = atomicAdd(&s.u[0], __popc(wm));
+                                base = __shfl_sync(0xffffffffu, base, __ffs(wm) - 1);
+                                if (want) s.buf[base + __popc(wm & ((1u << lane) - 1u))] = key;
+                            }
                         }
                     }
                     __syncthreads();
@@ -502,7 +529,7 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
 }
 
 template <int NT, int RW>
-__global__ void __launch_bounds__(NT, 2048 / NT)
+__global__ void __launch_bounds__(NT, 1024 / NT)
 k_query(QArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -512,8 +539,8 @@ k_query(QArgs a)
         if (kq > a.k_max) kq = a.k_max;
         zero_query_state<NT>(a, s);
         __syncthreads();
-        if (kq > 0) gather_counts<NT>(a, s, a.qb + size_t(q) * a.L);
-        decode_topk<NT, RW>(a, s, q, kq);
+        if (kq > 0) gather_counts<NT, kPlainUnroll>(a, s, a.qb + size_t(q) * a.L);
+        decode_topk<NT, RW, kPlainUnroll>(a, s, q, kq);
     }
 }
 
@@ -838,20 +865,28 @@ int query_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
                  const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
                  uint8_t *out_scores)
 {
-    constexpr int NT = 256;
     if (nq == 0) return FLINNG_OK;
     QArgs a = make_args(ix, qbuckets, nq);
     a.k = k;
     a.k_max = k_max;
     a.out_ids = out_ids;
     a.out_scores = out_scores;
+    // CTA size: when shared memory admits only one or two CTAs per SM (large
+    // B*R), wider CTAs keep about 1,024 threads per SM decoding
+    int NT = 256;
     size_t smem;
     pick_buffer(a, NT, nullptr, 0, &smem);
+    const size_t fit = (228 * 1024) / (smem + 1024);
+    if (fit < 4) {
+        NT = fit < 2 ? 1024 : 512;
+        pick_buffer(a, NT, nullptr, 0, &smem);
+    }
     if (smem > 227 * 1024)
         return set_error(FLINNG_ERR_INVALID_ARG,
                          "query: k_max=%u with B*R=%u needs %zu bytes of shared memory (> 227 KB)",
                          k_max, a.BR, smem);
-    const void *fn = plain_kernel<NT>(ix->rw);
+    const void *fn = NT == 1024 ? plain_kernel<1024>(ix->rw)
+                     : NT == 512 ? plain_kernel<512>(ix->rw) : plain_kernel<256>(ix->rw);
     if (smem > 48 * 1024)
         FL_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     void *args[] = {&a};
