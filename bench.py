@@ -437,12 +437,12 @@ def dense_source(F, idx_id, h_q, share, keep):
 # --------------------------------------------------------------------------
 
 # Grids follow the paper's hyperparameter search (R in {2, 3, 4}, B and the
-# table count in powers of two, B * R < 2^16), capped by 8-bit counts (L <= 255)
-# and by L * R * N < 2^32 entries.
+# table count L (the paper's m) in powers of two up to 2^11, B * R < 2^16),
+# capped by L * R * N < 2^32 entries.
 SWEEPS = {
-    "C1": dict(R=(2, 3), B=(100, 1000, 5000), L=(16, 64, 255), K=(8, 12, 16)),
-    "C2": dict(R=(2, 3), B=(1000, 4096, 16384), L=(32, 64, 128, 255), K=(1, 2)),
-    "C3": dict(R=(2, 4), B=(5000, 16000), L=(64, 128, 255), K=(1,)),
+    "C1": dict(R=(2, 3), B=(100, 1000, 5000), L=(16, 64, 255, 1024), K=(8, 12, 16)),
+    "C2": dict(R=(2, 3), B=(1000, 4096, 16384), L=(32, 64, 128, 255, 512, 1024, 2048), K=(1,)),
+    "C3": dict(R=(2, 4), B=(5000, 16000), L=(64, 255, 1024), K=(1,)),
     "C4": dict(R=(3,), B=(20000,), L=(64, 128), K=(12, 16)),
 }
 
@@ -633,7 +633,7 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     # ---- query buffers (device)
     qb = torch.empty((nq, L), dtype=torch.int32, device=dev)
     ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
-    sc = torch.empty((nq, k), dtype=torch.uint8, device=dev)
+    sc = torch.empty((nq, k), dtype=torch.int16, device=dev)
     p_ids = torch.empty_like(ids)
     p_sc = torch.empty_like(sc)
     fp, n_, devflag, keep = ix._points(d_q)

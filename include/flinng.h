@@ -63,7 +63,7 @@ typedef struct flinng_config {
     uint32_t dim;           /* cosine: vector length d (1..65536); ignored for sets */
     uint32_t R;             /* repetitions, 1..8 (Sec. 3.1) */
     uint32_t B;             /* groups per repetition, B * R <= 65536 (Sec. 3.1) */
-    uint32_t L;             /* hash tables = Bloom-filter arrays, 1..255 (paper: m) */
+    uint32_t L;             /* hash tables = Bloom-filter arrays, 1..4095 (paper: m) */
     uint32_t K;             /* hashes concatenated per table (paper: L, Sec. 3.2);
                                SRP: 1..30 (it is also W) */
     uint32_t range_bits;    /* W: buckets per table = 2^W; SRP requires W == K;
@@ -152,13 +152,13 @@ int flinng_insert(flinng_index *idx, const flinng_points *pts, uint64_t n,
  * k: per-query result counts (nq entries, each <= k_max), or NULL for k_max
  * for every query. k_max <= 1024.
  * out_ids: nq x k_max point ids, padded with 0xFFFFFFFF.
- * out_scores: nq x k_max, the score of each returned point (the least count
- * among its R cells), padded with 0; may be NULL.
+ * out_scores: nq x k_max uint16, the score of each returned point (the least
+ * count among its R cells, 0..L), padded with 0; may be NULL.
  * Errors: INVALID_ARG (k > k_max, k_max > 1024, null outputs), CUDA.
  */
 int flinng_query(flinng_index *idx, const flinng_points *q, uint32_t nq,
                  const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
-                 uint8_t *out_scores, int on_device);
+                 uint16_t *out_scores, int on_device);
 
 /* Destroy the index and free its device memory. NULL is a no-op. */
 int flinng_destroy(flinng_index *idx);
@@ -224,15 +224,15 @@ int flinng_hash(flinng_index *idx, const flinng_points *pts, uint64_t n,
  */
 int flinng_query_buckets(flinng_index *idx, const uint32_t *qbuckets,
                          uint32_t nq, const uint32_t *k, uint32_t k_max,
-                         uint32_t *out_ids, uint8_t *out_scores,
+                         uint32_t *out_ids, uint16_t *out_scores,
                          int on_device);
 
 /*
  * Per-cell collision counts of nq queries given their buckets (Sec. 5):
- * out_counts nq x (B*R) uint8.
+ * out_counts nq x (B*R) uint16 (each in 0..L).
  */
 int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq,
-                  uint8_t *out_counts, int on_device);
+                  uint16_t *out_counts, int on_device);
 
 /*
  * Copy the index out to HOST buffers (synchronous).
@@ -295,7 +295,7 @@ uint64_t flinng_kernel_launches(void);
  */
 int flinng_query_noalloc(flinng_index *idx, const flinng_points *q, uint32_t nq,
                          const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
-                         uint8_t *out_scores);
+                         uint16_t *out_scores);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching over several resident indices             */
@@ -362,7 +362,7 @@ uint64_t flinng_server_device_bytes(const flinng_server *srv);
  * res: per-request times, status, index version and batch.
  * Errors: INVALID_ARG (bad request, checked before anything runs), CUDA. */
 int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_t n,
-                         uint32_t *out_ids, uint8_t *out_scores, flinng_request_result *res);
+                         uint32_t *out_ids, uint16_t *out_scores, flinng_request_result *res);
 
 /* Destroy the server (not its indices). NULL is a no-op. */
 int flinng_server_destroy(flinng_server *srv);

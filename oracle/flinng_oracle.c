@@ -320,7 +320,7 @@ int64_t oracle_build_csr(const uint32_t *bucket, const uint16_t *gid,
 /* cnt[c] = number of tables l whose list for the query's bucket holds c. */
 void oracle_counts(const uint32_t *off, const uint16_t *cells, uint32_t L,
                    uint32_t W, const uint32_t *qbucket, uint32_t BR,
-                   uint8_t *cnt)
+                   uint16_t *cnt)
 {
     for (uint32_t c = 0; c < BR; ++c) cnt[c] = 0;
     for (uint32_t l = 0; l < L; ++l) {
@@ -336,7 +336,7 @@ void oracle_counts(const uint32_t *off, const uint16_t *cells, uint32_t L,
  * qbucket[l]. For sampled queries on indices too large to rebuild here. */
 void oracle_counts_direct(const uint32_t *bucket, const uint16_t *gid,
                           uint64_t N, uint32_t L, uint32_t R, uint32_t B,
-                          const uint32_t *qbucket, uint8_t *cnt)
+                          const uint32_t *qbucket, uint16_t *cnt)
 {
     const uint32_t BR = B * R;
     uint8_t *hit = (uint8_t *)malloc(BR ? BR : 1);
@@ -355,7 +355,7 @@ void oracle_counts_direct(const uint32_t *bucket, const uint16_t *gid,
 /* A7-A9: Alg. 3, threshold relaxation                                       */
 /* ------------------------------------------------------------------------ */
 
-static const uint8_t *g_sort_cnt;
+static const uint16_t *g_sort_cnt;
 
 static int cmp_cell(const void *p, const void *q)
 {
@@ -372,11 +372,11 @@ static int cmp_cell(const void *p, const void *q)
  * Unused output slots get id 0xFFFFFFFF and score 0. Returns #results.
  * counts_scratch: N bytes (R <= 255).
  */
-static uint32_t alg3_one(const uint8_t *cnt, const uint64_t *moff,
+static uint32_t alg3_one(const uint16_t *cnt, const uint64_t *moff,
                          const uint32_t *mem, uint64_t N, uint32_t R,
                          uint32_t B, uint32_t k, uint32_t t_min,
                          uint8_t *counts, uint32_t *order,
-                         uint32_t *out_ids, uint8_t *out_scores, uint32_t k_max)
+                         uint32_t *out_ids, uint16_t *out_scores, uint32_t k_max)
 {
     const uint32_t BR = B * R;
     for (uint32_t i = 0; i < k_max; ++i) { out_ids[i] = 0xFFFFFFFFu; out_scores[i] = 0; }
@@ -412,10 +412,10 @@ int oracle_query(const uint32_t *off, const uint16_t *cells, uint32_t L,
                  uint32_t W, const uint64_t *moff, const uint32_t *mem,
                  uint64_t N, uint32_t R, uint32_t B, uint32_t t_min,
                  const uint32_t *qbucket, uint64_t nq, const uint32_t *k,
-                 uint32_t k_max, uint32_t *out_ids, uint8_t *out_scores)
+                 uint32_t k_max, uint32_t *out_ids, uint16_t *out_scores)
 {
     const uint32_t BR = B * R;
-    uint8_t *cnt = (uint8_t *)malloc(BR ? BR : 1);
+    uint16_t *cnt = (uint16_t *)malloc(sizeof(uint16_t) * (BR ? BR : 1));
     uint8_t *counts = (uint8_t *)malloc(N ? N : 1);
     uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * (BR ? BR : 1));
     int rc = 0;
@@ -433,10 +433,10 @@ int oracle_query(const uint32_t *off, const uint16_t *cells, uint32_t L,
 }
 
 /* Alg. 3 from given counts (used by tests to drive the decode directly). */
-uint32_t oracle_alg3(const uint8_t *cnt, const uint64_t *moff,
+uint32_t oracle_alg3(const uint16_t *cnt, const uint64_t *moff,
                      const uint32_t *mem, uint64_t N, uint32_t R, uint32_t B,
                      uint32_t k, uint32_t t_min, uint32_t *out_ids,
-                     uint8_t *out_scores, uint32_t k_max)
+                     uint16_t *out_scores, uint32_t k_max)
 {
     uint8_t *counts = (uint8_t *)malloc(N ? N : 1);
     uint32_t *order = (uint32_t *)malloc(sizeof(uint32_t) * ((B * R) != 0 ? (B * R) : 1));

@@ -65,17 +65,17 @@ def lib():
                                        C.c_uint32, C.c_uint32, u32, u16, C.c_uint64]
         L.oracle_build_csr.restype = C.c_int64
         L.oracle_counts.argtypes = [u32, u16, C.c_uint32, C.c_uint32, u32,
-                                    C.c_uint32, u8]
+                                    C.c_uint32, u16]
         L.oracle_counts.restype = None
         L.oracle_query.argtypes = [u32, u16, C.c_uint32, C.c_uint32, u64, u32,
                                    C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
-                                   u32, C.c_uint64, C.c_void_p, C.c_uint32, u32, u8]
+                                   u32, C.c_uint64, C.c_void_p, C.c_uint32, u32, u16]
         L.oracle_query.restype = C.c_int
         L.oracle_counts_direct.argtypes = [u32, u16, C.c_uint64, C.c_uint32, C.c_uint32,
-                                           C.c_uint32, u32, u8]
+                                           C.c_uint32, u32, u16]
         L.oracle_counts_direct.restype = None
-        L.oracle_alg3.argtypes = [u8, u64, u32, C.c_uint64, C.c_uint32, C.c_uint32,
-                                  C.c_uint32, C.c_uint32, u32, u8, C.c_uint32]
+        L.oracle_alg3.argtypes = [u16, u64, u32, C.c_uint64, C.c_uint32, C.c_uint32,
+                                  C.c_uint32, C.c_uint32, u32, u16, C.c_uint32]
         L.oracle_alg3.restype = C.c_uint32
         _lib = L
     return _lib
@@ -167,7 +167,7 @@ def build_csr(buckets, gid, B: int, W: int):
 
 
 def counts(off, cells, L: int, W: int, qbucket, BR: int):
-    cnt = np.zeros(BR, np.uint8)
+    cnt = np.zeros(BR, np.uint16)
     cells = _c(cells, np.uint16) if len(cells) else np.zeros(1, np.uint16)
     lib().oracle_counts(_c(off, np.uint32), cells, L, W, _c(qbucket, np.uint32), BR, cnt)
     return cnt
@@ -179,7 +179,7 @@ def counts_direct(buckets, gid, B: int, qbucket):
     gid = _c(gid, np.uint16)
     N, L = buckets.shape
     R = gid.shape[1]
-    cnt = np.zeros(B * R, np.uint8)
+    cnt = np.zeros(B * R, np.uint16)
     lib().oracle_counts_direct(buckets, gid, N, L, R, B, _c(qbucket, np.uint32), cnt)
     return cnt
 
@@ -187,8 +187,8 @@ def counts_direct(buckets, gid, B: int, qbucket):
 def alg3(cnt, moff, mem, N: int, R: int, B: int, k: int, t_min: int = 1, k_max=None):
     k_max = k if k_max is None else k_max
     ids = np.zeros(max(k_max, 1), np.uint32)
-    sc = np.zeros(max(k_max, 1), np.uint8)
-    n = lib().oracle_alg3(_c(cnt, np.uint8), _c(moff, np.uint64), _c(mem, np.uint32),
+    sc = np.zeros(max(k_max, 1), np.uint16)
+    n = lib().oracle_alg3(_c(cnt, np.uint16), _c(moff, np.uint64), _c(mem, np.uint32),
                           N, R, B, k, t_min, ids, sc, k_max)
     return ids[:k_max], sc[:k_max], int(n)
 
@@ -233,7 +233,7 @@ class OracleIndex:
         qb = _c(qb, np.uint32)
         nq = qb.shape[0]
         ids = np.zeros((nq, max(k_max, 1)), np.uint32)
-        sc = np.zeros((nq, max(k_max, 1)), np.uint8)
+        sc = np.zeros((nq, max(k_max, 1)), np.uint16)
         kk = _c(k, np.uint32) if k is not None else None
         cells = self.cells if len(self.cells) else np.zeros(1, np.uint16)
         rc = lib().oracle_query(self.off, cells, self.L, self.W, self.moff, self.mem,

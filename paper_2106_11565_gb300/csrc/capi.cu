@@ -83,7 +83,7 @@ int check_config(const flinng_config *c, const flinng_params *p)
     if (c->R < 1 || c->R > 8) return set_error(FLINNG_ERR_INVALID_ARG, "create: R must be in 1..8");
     if (c->B < 1 || uint64_t(c->B) * c->R > 65536)
         return set_error(FLINNG_ERR_INVALID_ARG, "create: need 1 <= B and B*R <= 65536");
-    if (c->L < 1 || c->L > 255) return set_error(FLINNG_ERR_INVALID_ARG, "create: L must be in 1..255");
+    if (c->L < 1 || c->L > kMaxL) return set_error(FLINNG_ERR_INVALID_ARG, "create: L must be in 1..%u", kMaxL);
     if (c->K < 1) return set_error(FLINNG_ERR_INVALID_ARG, "create: K must be >= 1");
     if (c->range_bits < 1 || c->range_bits > 30 || (uint64_t(c->L) << c->range_bits) >= (1ull << 31))
         return set_error(FLINNG_ERR_INVALID_ARG, "create: need 1 <= W <= 30 and L*2^W < 2^31");
@@ -279,6 +279,7 @@ int flinng_create(const flinng_config *cfg, const flinng_params *params, void *s
     ix->P = L * K;
     ix->rp = R == 1 ? 1 : R == 2 ? 2 : R <= 4 ? 4 : 8;
     ix->rw = R == 1 ? 1 : R <= 3 ? 2 : R <= 7 ? 4 : 8;
+    ix->cw = cfg->L <= 255 ? 1 : 2;
     ix->BR = cfg->B * R;
     ix->BRw = (ix->BR + 31) / 32;
     // a heavy slot's bitmap (B*R bits) is no larger than its list (2 bytes a cell)
@@ -395,13 +396,13 @@ int flinng_tune_query(flinng_index *idx, const flinng_points *q, uint32_t nq, ui
     FL_TRY(check_points(idx, q, nq, on_device));
     const cudaStream_t st = idx->stream;
     const size_t need = 4096 + stage_bytes(idx, q, nq, on_device) + carve_bytes<uint32_t>(uint64_t(nq) * k_max) +
-                        carve_bytes<uint8_t>(uint64_t(nq) * k_max);
+                        carve_bytes<uint16_t>(uint64_t(nq) * k_max);
     FL_TRY(ws_reserve(idx, need));
     Carver c(idx->ws.ptr, idx->ws.bytes);
     Staged fs;
     FL_TRY(stage_points(idx, q, nq, on_device, c, fs));
     uint32_t *ids = c.take<uint32_t>(uint64_t(nq) * k_max);
-    uint8_t *sc = c.take<uint8_t>(uint64_t(nq) * k_max);
+    uint16_t *sc = c.take<uint16_t>(uint64_t(nq) * k_max);
     FusedQuery fq{nq, fs.x, fs.ld, fs.off, fs.elems};
     cudaEvent_t e0, e1;
     FL_CUDA(cudaEventCreate(&e0));
@@ -507,7 +508,7 @@ int flinng_hash(flinng_index *idx, const flinng_points *pts, uint64_t n, uint32_
 
 static int query_common(flinng_index *idx, const flinng_points *q, const uint32_t *qbuckets,
                         uint32_t nq, const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
-                        uint8_t *out_scores, int on_device)
+                        uint16_t *out_scores, int on_device)
 {
     if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
     if (k_max > kMaxKMax) return set_error(FLINNG_ERR_INVALID_ARG, "query: k_max > %u", kMaxKMax);
@@ -524,7 +525,7 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
     if (q) need += stage_bytes(idx, q, nq, on_device) + hash_ws_bytes(idx, nq);
     if (!on_device)
         need += carve_bytes<uint32_t>(nq) + carve_bytes<uint32_t>(uint64_t(nq) * k_max) +
-                carve_bytes<uint8_t>(uint64_t(nq) * k_max);
+                carve_bytes<uint16_t>(uint64_t(nq) * k_max);
     FL_TRY(ws_reserve(idx, need));
     Carver c(idx->ws.ptr, idx->ws.bytes);
     uint32_t *qb = nullptr;
@@ -551,7 +552,7 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
     }
     const uint32_t *dk = k;
     uint32_t *dids = out_ids;
-    uint8_t *dsc = out_scores;
+    uint16_t *dsc = out_scores;
     if (!on_device) {
         if (k) {
             uint32_t *t = c.take<uint32_t>(nq);
@@ -559,7 +560,7 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
             dk = t;
         }
         dids = c.take<uint32_t>(uint64_t(nq) * k_max);
-        dsc = out_scores ? c.take<uint8_t>(uint64_t(nq) * k_max) : nullptr;
+        dsc = out_scores ? c.take<uint16_t>(uint64_t(nq) * k_max) : nullptr;
     }
     if (fused) {
         FusedQuery fq{nq, fs.x, fs.ld, fs.off, fs.elems};
@@ -577,7 +578,9 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
     if (!on_device) {
         if (k_max) {
             FL_CUDA(cudaMemcpyAsync(out_ids, dids, uint64_t(nq) * k_max * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-            if (out_scores) FL_CUDA(cudaMemcpyAsync(out_scores, dsc, uint64_t(nq) * k_max, cudaMemcpyDeviceToHost, st));
+            if (out_scores)
+                FL_CUDA(cudaMemcpyAsync(out_scores, dsc, uint64_t(nq) * k_max * sizeof(uint16_t),
+                                        cudaMemcpyDeviceToHost, st));
         }
         FL_CUDA(cudaStreamSynchronize(st));
     }
@@ -585,20 +588,20 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
 }
 
 int flinng_query(flinng_index *idx, const flinng_points *q, uint32_t nq, const uint32_t *k,
-                 uint32_t k_max, uint32_t *out_ids, uint8_t *out_scores, int on_device)
+                 uint32_t k_max, uint32_t *out_ids, uint16_t *out_scores, int on_device)
 {
     if (nq > 0 && !q) return set_error(FLINNG_ERR_INVALID_ARG, "query: q is null");
     return query_common(idx, q, nullptr, nq, k, k_max, out_ids, out_scores, on_device);
 }
 
 int flinng_query_buckets(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq, const uint32_t *k,
-                         uint32_t k_max, uint32_t *out_ids, uint8_t *out_scores, int on_device)
+                         uint32_t k_max, uint32_t *out_ids, uint16_t *out_scores, int on_device)
 {
     if (nq > 0 && !qbuckets) return set_error(FLINNG_ERR_INVALID_ARG, "query: qbuckets is null");
     return query_common(idx, nullptr, qbuckets, nq, k, k_max, out_ids, out_scores, on_device);
 }
 
-int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq, uint8_t *out_counts,
+int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq, uint16_t *out_counts,
                   int on_device)
 {
     if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
@@ -607,13 +610,13 @@ int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq, uint
     const cudaStream_t st = idx->stream;
     const uint32_t L = idx->cfg.L, BR = idx->BR;
     if (on_device) return counts_launch(idx, qbuckets, nq, out_counts);
-    FL_TRY(ws_reserve(idx, carve_bytes<uint32_t>(uint64_t(nq) * L) + carve_bytes<uint8_t>(uint64_t(nq) * BR) + 1024));
+    FL_TRY(ws_reserve(idx, carve_bytes<uint32_t>(uint64_t(nq) * L) + carve_bytes<uint16_t>(uint64_t(nq) * BR) + 1024));
     Carver c(idx->ws.ptr, idx->ws.bytes);
     uint32_t *qb = c.take<uint32_t>(uint64_t(nq) * L);
-    uint8_t *oc = c.take<uint8_t>(uint64_t(nq) * BR);
+    uint16_t *oc = c.take<uint16_t>(uint64_t(nq) * BR);
     FL_CUDA(cudaMemcpyAsync(qb, qbuckets, uint64_t(nq) * L * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     FL_TRY(counts_launch(idx, qb, nq, oc));
-    FL_CUDA(cudaMemcpyAsync(out_counts, oc, uint64_t(nq) * BR, cudaMemcpyDeviceToHost, st));
+    FL_CUDA(cudaMemcpyAsync(out_counts, oc, uint64_t(nq) * BR * sizeof(uint16_t), cudaMemcpyDeviceToHost, st));
     FL_CUDA(cudaStreamSynchronize(st));
     return FLINNG_OK;
 }

@@ -51,7 +51,7 @@ using namespace flinng;
 
 extern "C" int flinng_query_noalloc(flinng_index *idx, const flinng_points *q, uint32_t nq,
                                     const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
-                                    uint8_t *out_scores)
+                                    uint16_t *out_scores)
 {
     if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
     if (k_max > kMaxKMax) return set_error(FLINNG_ERR_INVALID_ARG, "query_noalloc: k_max > %u", kMaxKMax);

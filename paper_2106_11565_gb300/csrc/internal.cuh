@@ -12,6 +12,7 @@ namespace flinng {
 constexpr uint32_t kEmpty32 = 0xFFFFFFFFu;
 constexpr uint64_t kKeyNone = ~0ull;
 constexpr uint32_t kMaxKMax = 1024;
+constexpr uint32_t kMaxL = 4095;          // 12-bit scores in the query keys
 constexpr uint32_t kDophMaxAttempts = 4096;
 // hash counters: [0] undecided after the first pass, [1] exact accumulator,
 // [2] fp64 re-checks, [3] compensated fp32 re-checks, [4] first-pass signs
@@ -101,6 +102,7 @@ struct flinng_index {
     uint32_t P;            // L * K projections / MinHash values per point
     uint32_t rp;           // gid row stride (R rounded up to 1, 2, 4 or 8)
     uint32_t rw;           // words per repetition-0 member record (1, 2, 4 or 8)
+    uint32_t cw;           // bytes per per-cell count in the query kernels: 1 (L <= 255) or 2
     uint32_t BR;
     uint64_t nslot;        // L << W
     uint64_t entries_cap;  // L * R * capacity
@@ -186,14 +188,14 @@ struct FusedQuery {
     const uint32_t *elems;
 };
 int query_fused_launch(flinng_index *ix, const FusedQuery &fq, const uint32_t *k, uint32_t k_max,
-                       uint32_t *out_ids, uint8_t *out_scores, const QueryTuning *tune);
+                       uint32_t *out_ids, uint16_t *out_scores, const QueryTuning *tune);
 int query_graph_launch(flinng_index *ix, const FusedQuery &fq, const uint32_t *k, uint32_t k_max,
-                       uint32_t *out_ids, uint8_t *out_scores, const QueryTuning *tune);
+                       uint32_t *out_ids, uint16_t *out_scores, const QueryTuning *tune);
 void destroy_graphs(flinng_index *ix);
 int query_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
                  const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
-                 uint8_t *out_scores);
+                 uint16_t *out_scores);
 int counts_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
-                  uint8_t *out_counts);
+                  uint16_t *out_counts);
 
 }  // namespace flinng

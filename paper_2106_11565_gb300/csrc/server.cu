@@ -89,7 +89,7 @@ Layout layout_for(const flinng_server *srv)
     // re-check lists (fp32 path) or the tensor-core split operands and lists
     L.srp = (size_t)c.take<unsigned long long>(2 * nb * srv->max_P + 64 + nb * srv->max_dim / 2 + nb + 1024);
     L.ids = (size_t)c.take<uint32_t>(nb * km);
-    L.sc = (size_t)c.take<uint8_t>(nb * km);
+    L.sc = (size_t)c.take<uint16_t>(nb * km);
     L.total = c.used + 256;
     return L;
 }
@@ -163,7 +163,7 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
     int rc = FLINNG_OK;
     const uint32_t *dk = reinterpret_cast<const uint32_t *>(d + Lo.k);
     uint32_t *dids = reinterpret_cast<uint32_t *>(d + Lo.ids);
-    uint8_t *dsc = reinterpret_cast<uint8_t *>(d + Lo.sc);
+    uint16_t *dsc = reinterpret_cast<uint16_t *>(d + Lo.sc);
     const bool big_srp = srp && uint64_t(ix->P) * ix->cfg.dim > (1ull << 18);
     if (big_srp) {
         uint32_t *qb = reinterpret_cast<uint32_t *>(d + Lo.qb);
@@ -184,7 +184,8 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
     FL_TRY(rc);
     FL_CUDA(cudaMemcpyAsync(h + Lo.ids, d + Lo.ids, size_t(nb) * km * sizeof(uint32_t), cudaMemcpyDeviceToHost,
                             slot.stream));
-    FL_CUDA(cudaMemcpyAsync(h + Lo.sc, d + Lo.sc, size_t(nb) * km, cudaMemcpyDeviceToHost, slot.stream));
+    FL_CUDA(cudaMemcpyAsync(h + Lo.sc, d + Lo.sc, size_t(nb) * km * sizeof(uint16_t), cudaMemcpyDeviceToHost,
+                            slot.stream));
     FL_CUDA(cudaEventRecord(slot.done, slot.stream));
     return FLINNG_OK;
 }
@@ -267,7 +268,7 @@ int flinng_server_add_index(flinng_server *srv, flinng_index *ix, uint32_t *inde
 uint64_t flinng_server_device_bytes(const flinng_server *srv) { return srv ? srv->bytes_used : 0; }
 
 int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_t n, uint32_t *out_ids,
-                         uint8_t *out_scores, flinng_request_result *res)
+                         uint16_t *out_scores, flinng_request_result *res)
 {
     if (!srv || (n && (!reqs || !out_ids || !res))) return set_error(FLINNG_ERR_INVALID_ARG, "replay: null argument");
     const uint32_t km = srv->cfg.k_max;
@@ -316,7 +317,8 @@ int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_
             for (size_t i = 0; i < s.reqs.size(); ++i) {
                 const uint64_t r = s.reqs[i];
                 std::memcpy(out_ids + r * km, h + Lo.ids + i * km * sizeof(uint32_t), km * sizeof(uint32_t));
-                if (out_scores) std::memcpy(out_scores + r * km, h + Lo.sc + i * km, km);
+                if (out_scores)
+                    std::memcpy(out_scores + r * km, h + Lo.sc + i * km * sizeof(uint16_t), km * sizeof(uint16_t));
                 res[r].t_done = t;
                 res[r].status = FLINNG_OK;
             }

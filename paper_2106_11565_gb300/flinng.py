@@ -277,7 +277,8 @@ class Index:
     def _out(self, dev, shape, dt):
         if dev:
             import torch
-            tdt = {np.uint32: torch.int32, np.uint8: torch.uint8, np.float32: torch.float32}[dt]
+            tdt = {np.uint32: torch.int32, np.uint16: torch.int16, np.uint8: torch.uint8,
+                   np.float32: torch.float32}[dt]
             return torch.empty(shape, dtype=tdt, device="cuda")
         return np.zeros(shape, dt)
 
@@ -293,7 +294,7 @@ class Index:
     def query(self, q, k_max: int, k=None):
         fp, nq, dev, keep = self._points(q)
         ids = self._out(dev, (nq, k_max), np.uint32)
-        sc = self._out(dev, (nq, k_max), np.uint8)
+        sc = self._out(dev, (nq, k_max), np.uint16)
         kk = None if k is None else (k if _is_cuda(k) else _np(k, np.uint32))
         _check(self.lib.flinng_query(self.h, C.byref(fp), nq, _ptr(kk), k_max, _ptr(ids), _ptr(sc), dev))
         return ids, sc
@@ -303,7 +304,7 @@ class Index:
         qb = qb if dev else _np(qb, np.uint32)
         nq = qb.shape[0]
         ids = self._out(dev, (nq, k_max), np.uint32)
-        sc = self._out(dev, (nq, k_max), np.uint8)
+        sc = self._out(dev, (nq, k_max), np.uint16)
         kk = None if k is None else (k if _is_cuda(k) else _np(k, np.uint32))
         _check(self.lib.flinng_query_buckets(self.h, _ptr(qb), nq, _ptr(kk), k_max, _ptr(ids),
                                              _ptr(sc), dev))
@@ -312,7 +313,7 @@ class Index:
     def counts(self, qb):
         dev = int(_is_cuda(qb))
         qb = qb if dev else _np(qb, np.uint32)
-        out = self._out(dev, (qb.shape[0], self.B * self.R), np.uint8)
+        out = self._out(dev, (qb.shape[0], self.B * self.R), np.uint16)
         _check(self.lib.flinng_counts(self.h, _ptr(qb), qb.shape[0], _ptr(out), dev))
         return out
 
@@ -394,7 +395,7 @@ class Server:
         input, a numpy array of RES_DTYPE for numpy input."""
         n = len(reqs)
         ids = np.zeros((max(n, 1), self.k_max), np.uint32)
-        sc = np.zeros((max(n, 1), self.k_max), np.uint8)
+        sc = np.zeros((max(n, 1), self.k_max), np.uint16)
         if isinstance(reqs, np.ndarray):
             assert reqs.dtype == REQ_DTYPE and reqs.flags.c_contiguous
             res = np.zeros(max(n, 1), RES_DTYPE)

@@ -381,3 +381,30 @@ def test_heavy_bucket_bitmaps(F, mode):
     ids, sc = jx.query(q2, 25)
     oids, osc = o2.query(q2, 25)
     assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("L,K,W,B", [(300, 1, 17, 1000), (1024, 1, 12, 250), (600, 2, 3, 60)])
+def test_wide_counts_bit_exact(F, mode, L, K, W, B):
+    """More than 255 tables: 16-bit counts and 60-bit keys. Scores above 255,
+    heavy buckets (W = 3: every list is long) and light ones, all modes."""
+    N, nq, R = 3000, 60, 2
+    pts, q, dp, perm = sets_case(70 + L, N, nq, R, L, K)
+    ix = F.Index("jaccard", R, B, L, K, capacity=N, params=dp, W=W)
+    ix.set_query_mode(mode)
+    ix.build(pts, perm)
+    o = oracle_index("jaccard", R, B, L, K, W, dp, pts, perm)
+    qb = ix.hash(q)[0]
+    got = ix.counts(qb)
+    for i in range(0, nq, 7):
+        assert np.array_equal(got[i], O.counts(o.off, o.cells, L, W, u32(qb)[i], B * R))
+    ids, sc = ix.query(q, 50)
+    oids, osc = o.query(q, 50)
+    assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)
+    # queries equal to indexed points: score L > 255 (no false negative)
+    pq = WL.csr_from_rows([pts[1][pts[0][i]:pts[0][i + 1]] for i in range(5)])
+    ids, sc = ix.query(pq, 20)
+    oids, osc = o.query(pq, 20)
+    assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)
+    for i in range(5):
+        assert sc[i, 0] == L

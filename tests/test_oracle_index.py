@@ -250,3 +250,39 @@ def test_counts_direct_equals_index_walk(seed):
     for _ in range(5):
         q = rng.integers(0, 1 << W, size=L).astype(np.uint32)
         assert np.array_equal(O.counts(off, cells, L, W, q, B * R), O.counts_direct(buckets, gid, B, q))
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_alg3_equals_closed_key_wide_counts(seed):
+    """Counts above 255 (L up to 4095 tables): the literal Alg. 3 and the
+    closed key still agree, so 16-bit counts order cells exactly."""
+    rng = np.random.default_rng(1000 + seed)
+    N = int(rng.integers(1, 65))
+    R = int(rng.integers(1, 5))
+    B = int(rng.integers(1, N + 1))
+    L = int(rng.choice([256, 300, 1024, 4095]))
+    gid = O.groups(WL.group_permutations(seed, R, N), B)
+    moff, mem = O.members(gid, B)
+    cnt = rng.integers(0, L + 1, size=B * R).astype(np.uint16)
+    cnt[rng.integers(0, B * R)] = L
+    for k in (1, 3, N):
+        for t_min in (1, 256, L):
+            ids, sc, n = O.alg3(cnt, moff, mem, N, R, B, k=k, t_min=t_min)
+            e_ids, e_sc = closed_key_order(cnt, gid, B, k, t_min)
+            assert ids[:n].tolist() == e_ids and sc[:n].tolist() == e_sc
+
+
+def test_counts_wide_equal_direct_definition():
+    """L = 300 tables: the reverse-index walk and the index-free definition
+    give the same counts, above 255 where every table collides."""
+    seed, N, L, K, R, B = 5, 200, 300, 1, 2, 10
+    rng = np.random.default_rng(seed)
+    buckets = rng.integers(0, 4, size=(N, L)).astype(np.uint32)   # 2-bit buckets: dense collisions
+    gid = O.groups(WL.group_permutations(seed, R, N), B)
+    off, cells = O.build_csr(buckets, gid, B, 2)
+    for i in range(5):
+        qb = buckets[i]
+        c1 = O.counts(off, cells, L, 2, qb, B * R)
+        c2 = O.counts_direct(buckets, gid, B, qb)
+        assert np.array_equal(c1, c2)
+        assert c1.max() == L and c1.dtype == np.uint16

@@ -22,7 +22,7 @@ def _noalloc(F, ix, pts_dev, nq, k_max):
     fp, n, dev, keep = ix._points(pts_dev)
     assert dev == 1 and n == nq
     ids = torch.full((nq, k_max), 7, dtype=torch.int32, device="cuda")
-    sc = torch.full((nq, k_max), 7, dtype=torch.uint8, device="cuda")
+    sc = torch.full((nq, k_max), 7, dtype=torch.int16, device="cuda")
     rc = F.load().flinng_query_noalloc(ix.h, C.byref(fp), nq, None, k_max, ids.data_ptr(), sc.data_ptr())
     assert rc == F.OK, F.load().flinng_last_error()
     torch.cuda.synchronize()
