@@ -338,7 +338,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("query.cu", "internal.cuh"):
+    for f in ("query.cu", "query_impl.cuh", "query_c16.cu", "internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2106_11565_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -445,6 +445,116 @@ SWEEPS = {
     "C3": dict(R=(2, 4), B=(5000, 16000), L=(64, 255, 1024), K=(1,)),
     "C4": dict(R=(3,), B=(20000,), L=(64, 128), K=(12, 16)),
 }
+
+
+def serving_runs(F, ix, c: dict, plain_qps: float, factors, check_sample: int = 0) -> dict:
+    """Poisson traces replayed by the C serving runtime on one resident index
+    at ``factors`` x the plain form's device-resident throughput; optionally
+    checks ``check_sample`` served results against the same query run alone."""
+    import torch
+    keep = []
+    k = max(100, c["k"])
+    srv = F.Server(hbm_budget=ix.device_bytes + (2 << 30), n_slots=8, max_batch=1024, k_max=k,
+                   max_batch_elems=1 << 21)
+    sid = srv.add_index(ix)
+    src = (sets_source(F, sid, c["q"], 1.0, keep) if c["metric"] != "cosine"
+           else dense_source(F, sid, torch.from_numpy(c["q"]).pin_memory().numpy(), 1.0, keep))
+    rng_t = np.random.default_rng([c["seed"], 77])
+    runs = {}
+    same = None
+    for f in factors:
+        rate = f * plain_qps
+        T = min(0.25, 1.5e6 / rate)
+        req = make_trace(F, rng_t, rate, T, [src])
+        l0 = F.kernel_launches()
+        ids_s, sc_s, res = srv.replay(req)
+        runs[f"{f}x_plain"] = dict(trace_stats(req, res, F), offered_qps=rate, duration_s=T,
+                                   gpu_launches=int(F.kernel_launches() - l0))
+        if check_sample and same is None:
+            # served rows equal the same request run alone on the index
+            pick = np.random.default_rng(5).choice(len(req), min(check_sample, len(req)), replace=False)
+            ok = True
+            for r in pick:
+                if c["metric"] != "cosine":
+                    # the request's own elements: n of them from its data pointer
+                    j, n = int((req["data"][r] - src["base"]) // 4), int(req["n"][r])
+                    one = (np.array([0, n], np.uint64), c["q"][1][j:j + n])
+                else:
+                    i = int((req["data"][r] - src["base"]) // (src["dim"] * 4))
+                    one = c["q"][i:i + 1]
+                rid, rsc = ix.query(one, k, k=np.array([req["k"][r]], np.uint32))
+                ok &= bool(np.array_equal(ids_s[r], rid[0]) and np.array_equal(sc_s[r], rsc[0]))
+            same = {"checked": int(len(pick)), "equal": ok}
+    srv.close()
+    out = {"form": "continuous batching (C runtime, 8 streams, batches <= 1024, host buffers)",
+           "plain_form_qps": plain_qps, "runs": runs,
+           "max_qps": max(r["achieved_qps"] for r in runs.values()),
+           "note": "offered load relative to the plain form's device-resident throughput; the serving "
+                   "path stages every request from host memory"}
+    if same is not None:
+        out["results_same_as_alone"] = same
+    return out
+
+
+def recall_target_point(F, c: dict, args, prec: int, dev, d_pts, d_q, tgt: dict, flush, ex_ids, ex_sims,
+                        smp) -> dict:
+    """The sweep's fastest point with recall@10 >= 0.9, measured like the main
+    run: the fused form through CUDA graphs, the plain batched form (hash kernel
+    then query kernel), and the serving form against the plain form."""
+    import torch
+    nq, k, N = c["nq"], c["k"], c["N"]
+    R, B, L, K, W = tgt["R"], tgt["B"], tgt["L"], tgt["K"], tgt["W"]
+    params = (WL.srp_projections(c["seed"], L * K, c["d"]) if c["metric"] == "cosine"
+              else WL.doph_params(c["seed"], L, K))
+    d_perm = torch.from_numpy(WL.group_permutations(c["seed"], R, N).view(np.int32)).to(dev)
+    ix = F.Index(c["metric"], R, B, L, K, capacity=N, params=params, dim=c.get("d", 0), W=W, precision=prec)
+    ix.build(d_pts, d_perm)
+    tuning = ix.tune(d_q, k)
+    ix.set_query_mode(F.QUERY_GRAPH)
+    stream = torch.cuda.current_stream()
+    fp, _, _, keepq = ix._points(d_q)
+    qb = torch.empty((nq, L), dtype=torch.int32, device=dev)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    sc = torch.empty((nq, k), dtype=torch.int16, device=dev)
+
+    def fused():
+        F._check(ix.lib.flinng_query(ix.h, C.byref(fp), nq, None, k, ids.data_ptr(), sc.data_ptr(), 1))
+
+    def plain():
+        F._check(ix.lib.flinng_hash(ix.h, C.byref(fp), nq, qb.data_ptr(), None, None, 1))
+        F._check(ix.lib.flinng_query_buckets(ix.h, qb.data_ptr(), nq, None, k, ids.data_ptr(),
+                                             sc.data_ptr(), 1))
+
+    def timed(fn):
+        for it in range(max(3, args.warmup)):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for it in range(args.steps):
+            flush.fill_(it + 1)
+            ev[it][0].record(stream)
+            fn()
+            ev[it][1].record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+    fused_ms = timed(fused)
+    got_f = ids.cpu().numpy().view(np.uint32)
+    plain_ms = timed(plain)
+    got_p = ids.cpu().numpy().view(np.uint32)
+    rec = recall_scores(c, got_f[smp], ex_ids, ex_sims)
+    out = {"params": {"R": R, "B": B, "L": L, "K": K, "W": W}, "tuning": tuning,
+           "recall": rec, "recall_target_met": rec["recall_at_10"] >= 0.9,
+           "fused_graph_qps": nq / (fused_ms / 1e3), "fused_ms_per_batch": fused_ms,
+           "plain_form_qps": nq / (plain_ms / 1e3), "plain_ms_per_batch": plain_ms,
+           "fused_equals_plain": bool(np.array_equal(got_f, got_p)),
+           "index_bytes": ix.device_bytes}
+    if not args.no_serving and not c.get("embed"):
+        sv = serving_runs(F, ix, c, out["plain_form_qps"], (0.5, 0.9, 2.0), check_sample=200)
+        out["serving"] = sv
+        out["serving_beats_plain"] = sv["max_qps"] > out["plain_form_qps"]
+    ix.close()
+    return out
 
 
 def recall_sweep(F, c: dict, name: str, prec: int, dev, d_pts, d_q, ex_ids, ex_sims, smp, flush,
@@ -752,28 +862,7 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     # ---- serving form on this index: Poisson traces through the C runtime
     serving = None
     if not args.no_serving and world == 1 and not c.get("embed"):
-        keep = []
-        srv = F.Server(hbm_budget=ix.device_bytes + (2 << 30), n_slots=8, max_batch=1024, k_max=max(100, k),
-                       max_batch_elems=1 << 21)
-        sid = srv.add_index(ix)
-        src = (sets_source(F, sid, c["q"], 1.0, keep) if c["metric"] != "cosine"
-               else dense_source(F, sid, torch.from_numpy(c["q"]).pin_memory().numpy(), 1.0, keep))
-        rng_t = np.random.default_rng([c["seed"], 77])
-        runs = {}
-        for f in (0.25, 0.5, 2.0):
-            rate = f * plain_value
-            T = min(0.25, 1.5e6 / rate)
-            req = make_trace(F, rng_t, rate, T, [src])
-            l0 = F.kernel_launches()
-            ids_s, sc_s, res = srv.replay(req)
-            runs[f"{f}x_plain"] = dict(trace_stats(req, res, F), offered_qps=rate, duration_s=T,
-                                       gpu_launches=int(F.kernel_launches() - l0))
-        srv.close()
-        serving = {"form": "continuous batching (C runtime, 8 streams, batches <= 1024, host buffers)",
-                   "plain_form_qps": plain_value, "runs": runs,
-                   "max_qps": runs["2.0x_plain"]["achieved_qps"],
-                   "note": "offered load relative to the plain form's device-resident throughput; the serving "
-                           "path stages every request from host memory, which bounds it at high rates"}
+        serving = serving_runs(F, ix, c, plain_value, (0.25, 0.5, 2.0))
 
     if rank != 0:
         return None
@@ -791,6 +880,10 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     if not args.no_recall and not args.no_sweep and args.workload in SWEEPS:
         sweep = recall_sweep(F, c, args.workload, prec, dev, d_pts, d_q, ex_ids, ex_sims, smp, flush,
                              steps=max(3, min(args.steps, 10)), warmup=max(3, args.warmup))
+    at_target = None
+    if sweep is not None and sweep["met"] and not c.get("embed"):
+        at_target = recall_target_point(F, c, args, prec, dev, d_pts, d_q, sweep["at_target"], flush,
+                                        ex_ids, ex_sims, smp)
     ex = ix.export(cells=False)
     qb_h = qb.cpu().numpy().view(np.uint32)
     n_acc = max(10, min(200, int(2e8 // (c["N"] * c["R"]))))
@@ -864,6 +957,7 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
         "recall": rec,
         "recall_target_met": rec["recall_at_10"] >= 0.9,
         "recall_sweep": sweep,
+        "at_recall_target": at_target,
         "latency_ms": {"batch_p50": pct(50), "batch_p99": pct(99),
                        "note": "plain batched form: every query of a batch completes with the batch"},
         "plain_form": {"value": plain_value, "unit": UNIT, "ms_per_step": statistics.mean(plain_ms),
@@ -1081,6 +1175,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-form traces")
     ap.add_argument("--no-recall", action="store_true", help="skip the exact ground truth (profiling runs)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the recall sweep over (R, B, L, K)")
+    ap.add_argument("--n-points", type=int, default=0,
+                    help="streamed embedding workload only: index this many points instead of the config's "
+                         "(small profiling cases; the line says so)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x2"],
                     help="SRP projection arithmetic for cosine workloads (signs are exact either way)")
     args = ap.parse_args()
@@ -1104,6 +1201,12 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
     c = make_workload(args.workload)
+    if args.n_points:
+        if not c.get("embed"):
+            raise SystemExit("--n-points applies to the streamed embedding workload (C4) only")
+        c["N"] = args.n_points
+        c["perm"] = WL.group_permutations(c["seed"], c["R"], c["N"])
+        c["desc"] = c["desc"].replace("N=10000000", f"N={args.n_points} (reduced with --n-points)")
     line = run_ours(args, c, rank, world)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)

@@ -321,15 +321,15 @@ __device__ uint64_t block_compact(const QSmem &s, uint32_t nbuf, uint32_t kk)
 // whole counter words and adds 4 bits (CW = 1) or 2 bits (CW = 2) at a time,
 // spread to the counters of the word by one multiply, without atomics. The
 // other tables' lists are flattened over the CTA and counted with shared-memory
-// atomics, U cell loads in flight per thread. Contains __syncthreads.
+// atomics, U cell loads in flight per thread. Expects s.u[5] == 0 (the heavy
+// table count, zeroed with the query state) and leaves it 0. Contains
+// __syncthreads.
 template <int NT, int CW, int U = 1>
 __device__ void gather_counts(const QArgs &a, const QSmem &s, const uint32_t *qb)
 {
     const int tid = threadIdx.x;
     const uint32_t nwords = q_count_words(a.BR, CW);
     for (uint32_t l0 = 0; l0 < a.L; l0 += NT) {
-        if (tid == 0) s.u[5] = 0u;
-        __syncthreads();
         const uint32_t l = l0 + tid;
         uint32_t beg = 0, len = 0;
         if (l < a.L) {
@@ -387,6 +387,8 @@ __device__ void gather_counts(const QArgs &a, const QSmem &s, const uint32_t *qb
                 else atomicAdd(&s.cntw[c[u] >> 1], 1u << ((c[u] & 1) * 16));
             }
         }
+        // every thread read nh before the heavy section's barrier (or nh was 0)
+        if (tid == 0) s.u[5] = 0u;
         __syncthreads();
     }
 }
@@ -420,20 +422,25 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
             if (v >= a.t_min) atomicAdd(&s.lvl_n[v], 1u);
         }
         __syncthreads();
-        {
-            // start of each level in descending level order: thread i takes
-            // the i-th run of consecutive levels from L down to t_min
+        if (tid < 32) {
+            // start of each level in descending level order, by one warp: lane
+            // i takes the i-th run of consecutive levels from L down to t_min
             const uint32_t nl = a.L - a.t_min + 1;
-            const uint32_t per = (nl + NT - 1) / NT;
+            const uint32_t per = (nl + 31) / 32;
             uint32_t local = 0;
             for (uint32_t i = 0; i < per; ++i) {
-                const uint32_t pos = uint32_t(tid) * per + i;
+                const uint32_t pos = uint32_t(lane) * per + i;
                 if (pos < nl) local += s.lvl_n[a.L - pos];
             }
-            uint32_t all;
-            uint32_t run = block_excl_scan<NT>(local, s.wsum, &all);
+            uint32_t incl = local;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            uint32_t run = incl - local;
             for (uint32_t i = 0; i < per; ++i) {
-                const uint32_t pos = uint32_t(tid) * per + i;
+                const uint32_t pos = uint32_t(lane) * per + i;
                 if (pos < nl) {
                     s.lvl_cur[a.L - pos] = run;
                     run += s.lvl_n[a.L - pos];
@@ -540,26 +547,38 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
         }
     }
     __syncthreads();
-    // final top-k: cut to kq keys, sort, write
+    // final top-k: cut to kq keys, order them, write
     const uint32_t nbuf = s.u[0];
     const uint32_t nk = nbuf < kq ? nbuf : kq;
     if (nbuf > kq) block_compact<NT, CW>(s, nbuf, kq);
-    for (uint32_t i = tid; i < a.kp; i += NT) s.keep[i] = (i < nk) ? s.buf[i] : kKeyNone;
-    __syncthreads();
-    for (uint32_t k2 = 2; k2 <= a.kp; k2 <<= 1) {
-        for (uint32_t j = k2 >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = tid; i < a.kp; i += NT) {
-                const uint32_t l = i ^ j;
-                if (l > i) {
-                    const uint64_t x = s.keep[i], y = s.keep[l];
-                    const bool up = (i & k2) == 0;
-                    if ((x > y) == up) {
-                        s.keep[i] = y;
-                        s.keep[l] = x;
+    if (nk <= 256) {
+        // rank sort: the keys are distinct, so a key's rank is the number of
+        // smaller keys; one barrier instead of a sorting network
+        for (uint32_t i = tid; i < nk; i += NT) {
+            const uint64_t x = s.buf[i];
+            uint32_t r = 0;
+            for (uint32_t j = 0; j < nk; ++j) r += s.buf[j] < x ? 1u : 0u;
+            s.keep[r] = x;
+        }
+        __syncthreads();
+    } else {
+        for (uint32_t i = tid; i < a.kp; i += NT) s.keep[i] = (i < nk) ? s.buf[i] : kKeyNone;
+        __syncthreads();
+        for (uint32_t k2 = 2; k2 <= a.kp; k2 <<= 1) {
+            for (uint32_t j = k2 >> 1; j > 0; j >>= 1) {
+                for (uint32_t i = tid; i < a.kp; i += NT) {
+                    const uint32_t l = i ^ j;
+                    if (l > i) {
+                        const uint64_t x = s.keep[i], y = s.keep[l];
+                        const bool up = (i & k2) == 0;
+                        if ((x > y) == up) {
+                            s.keep[i] = y;
+                            s.keep[l] = x;
+                        }
                     }
                 }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
     for (uint32_t i = tid; i < a.k_max; i += NT) {
@@ -825,6 +844,7 @@ k_counts(QArgs a)
     const uint32_t nwords = q_count_words(a.BR, CW);
     for (uint32_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
         for (uint32_t i = tid; i < nwords; i += NT) s.cntw[i] = 0u;
+        if (tid < 8) s.u[tid] = 0u;
         __syncthreads();
         gather_counts<NT, CW>(a, s, a.qb + size_t(q) * a.L);
         for (uint32_t c = tid; c < a.BR; c += NT) a.out_counts[size_t(q) * a.BR + c] = uint16_t(cnt_at<CW>(s, c));

@@ -23,9 +23,10 @@
 //   warp 0     TMA producer: 3-stage ring of {X1, X2, W1, W2} tiles of 128 rows
 //              x 64 bf16 (128-byte swizzle), one mbarrier per stage;
 //   warp 1     allocates 512 TMEM columns (two buffers of {hi, lo}); one elected
-//              thread issues the MMAs (M=128, N=128, K=16) of k-block s into
-//              buffer s % 2, then commits the stage back to the producer and the
-//              buffer to the epilogue;
+//              thread issues the MMAs of k-block s into buffer s % 2 - per 16-wide
+//              step x1 [w1 w2] (M=128, N=256: hi and the x1 w2 half of lo) and
+//              x2 w1 (N=128, into lo) - then commits the stage back to the
+//              producer and the buffer to the epilogue;
 //   warps 2-9  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +32 (one point per
 //              thread) and 64 of the 128 columns, drains each buffer into fp32
 //              registers and hands it back; at the end decides the signs,
@@ -119,19 +120,22 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
     return d;
 }
 
-// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major.
+// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major,
+// M = 128 rows, N columns.
+template <int N>
 __host__ __device__ constexpr uint32_t mma_idesc()
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kTN >> 3) << 17) | (uint32_t(kTM >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(kTM >> 4) << 24);
 }
 
+template <int N>
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(a), "l"(b), "r"(mma_idesc()), "r"(accumulate)
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(mma_idesc<N>()), "r"(accumulate)
         : "memory");
 }
 
@@ -141,18 +145,24 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+// 32 consecutive fp32 columns of this warp's 32 TMEM lanes; the caller waits
+// (tmem_wait_ld) before reading the registers.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32])
 {
-    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld()
+{
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 struct TcArgs {
@@ -191,7 +201,9 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
     uint32_t *abort_flag = tmem_slot + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t row0 = blockIdx.x * kTM, col0 = blockIdx.y * kTN;
+    // projection blocks vary fastest: the CTAs that share one X tile run in
+    // the same wave, so X is read from DRAM once and W stays in L2
+    const uint32_t row0 = blockIdx.y * kTM, col0 = blockIdx.x * kTN;
     const uint32_t nkb = (a.d + kTK - 1) / kTK;
 
     if (threadIdx.x == 0) {
@@ -252,17 +264,18 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t st = smem_u32(ring + s * kStageBytes);
                 const uint32_t t_hi = tmem + 256u * b, t_lo = t_hi + kTN;
+                // W1 and W2 tiles are adjacent in the stage, so [W1; W2] is one
+                // 256-row B operand: x1 [w1 w2] fills hi and lo in one MMA
+                // (N = 256), then x2 w1 adds into lo (N = 128)
 #pragma unroll
                 for (int kk = 0; kk < kTK / 16; ++kk) {
                     const uint32_t off = kk * 32;
                     const uint64_t x1 = smem_desc(st + 0 * kTileBytes + off);
                     const uint64_t x2 = smem_desc(st + 1 * kTileBytes + off);
-                    const uint64_t w1 = smem_desc(st + 2 * kTileBytes + off);
-                    const uint64_t w2 = smem_desc(st + 3 * kTileBytes + off);
+                    const uint64_t w12 = smem_desc(st + 2 * kTileBytes + off);
                     const uint32_t acc = kk > 0 ? 1u : 0u;     // each k-block starts a fresh pair
-                    mma_bf16(t_hi, x1, w1, acc);
-                    mma_bf16(t_lo, x1, w2, acc);
-                    mma_bf16(t_lo, x2, w1, 1u);
+                    mma_bf16<2 * kTN>(t_hi, x1, w12, acc);
+                    mma_bf16<kTN>(t_lo, x2, w12, 1u);
                 }
                 mma_commit(&empty[s]);
                 mma_commit(&tfull[b]);
@@ -290,17 +303,23 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // two halves of 32 columns: hi and lo loads in flight together, one
+            // wait each; the buffer goes back to the MMA issuer before the
+            // second half is added
+            uint32_t hv[32], lv[32];
+            tmem_ld32(tbase + 256u * b, hv);
+            tmem_ld32(tbase + 256u * b + kTN, lv);
+            tmem_wait_ld();
 #pragma unroll
-            for (int c0 = 0; c0 < 64; c0 += 16) {
-                float hi[16], lo[16];
-                tmem_ld16(tbase + 256u * b + c0, hi);
-                tmem_ld16(tbase + 256u * b + kTN + c0, lo);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) acc[c0 + j] += hi[j] + lo[j];
-            }
+            for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(hv[j]) + __uint_as_float(lv[j]);
+            tmem_ld32(tbase + 256u * b + 32, hv);
+            tmem_ld32(tbase + 256u * b + kTN + 32, lv);
+            tmem_wait_ld();
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[32 + j] += __uint_as_float(hv[j]) + __uint_as_float(lv[j]);
         }
         uint32_t ab = lane == 0 ? *(volatile uint32_t *)abort_flag : 0u;
         abort = abort || __shfl_sync(0xffffffffu, ab, 0) != 0u;    // warp-uniform
@@ -565,7 +584,7 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
         a.rlist = list1;
         a.rcount = cnt;
         a.err = ix->tc_err;
-        dim3 grid((unsigned)((rows + kTM - 1) / kTM), (P + kTN - 1) / kTN);
+        dim3 grid((P + kTN - 1) / kTN, (unsigned)((rows + kTM - 1) / kTM));
         k_srp_tc<<<grid, kTcThreads, smem, st>>>(mx1, mx2, mw1, mw2, a);
         count_launch();
         FL_CUDA(cudaGetLastError());
