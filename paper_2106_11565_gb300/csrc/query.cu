@@ -31,6 +31,8 @@ QArgs make_args(flinng_index *ix, const uint32_t *qb, uint32_t nq)
     a.B = ix->cfg.B;
     a.BR = ix->BR;
     a.t_min = ix->cfg.min_threshold;
+    a.avg_cell = uint32_t((ix->n_points + ix->cfg.B - 1) / ix->cfg.B);
+    a.gcells = 1;
     return a;
 }
 
@@ -49,6 +51,10 @@ void pick_buffer(QArgs &a, int NT, const QueryTuning *tune, size_t extra, size_t
         smem = qsmem_bytes(a.cap, a.kp, a.BR, a.B, NT, a.L, cw);
     }
     *smem_out = smem;
+    // a level group holds about one round of members
+    const uint32_t per = a.avg_cell ? a.avg_cell : 1u;
+    uint32_t g = (a.cap - a.kp) / per;
+    a.gcells = g < 1 ? 1u : (g > uint32_t(NT) ? uint32_t(NT) : g);
 }
 
 }  // namespace

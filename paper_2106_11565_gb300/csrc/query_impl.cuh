@@ -35,6 +35,7 @@ namespace flinng {
 
 constexpr int kQTmax = 256;              // CTA size of the counts kernel
 constexpr int kPlainUnroll = 4;          // plain kernel: loads in flight per thread
+constexpr uint32_t kRankSelectMax = 256; // compactions of at most this many keys rank them directly
 
 // key = (score_max - score) << 48 | lastcell << 32 | id
 template <int CW> struct CountWidth;
@@ -61,6 +62,8 @@ struct QArgs {
     const uint32_t *hidx;     // per slot: heavy bitmap index or kEmpty32
     const uint32_t *hbm;      // heavy slots' cell bitmaps, BRw words each
     uint32_t L, W, R, B, BR, BRw, t_min;
+    uint32_t gcells;   // cells per level group of the decode (at least 1)
+    uint32_t avg_cell; // members per repetition-0 cell, rounded up (host side, sizes gcells)
     uint32_t cap;      // candidate buffer entries (power of two)
     uint32_t kp;       // final sort width: power of two >= k_max
     uint32_t *out_ids;
@@ -72,7 +75,6 @@ struct QSmem {
     uint64_t *buf;       // cap candidate keys
     uint64_t *keep;      // kp keys (selection output, final sort)
     uint32_t *u;         // 8 scalars: nbuf, nkeep, digit, rank, whole, heavy tables, bound (u[6..7])
-    uint32_t *hist_s;    // nlev: points seen, by score
     uint32_t *lvl_n;     // nlev: repetition-0 cells per count
     uint32_t *lvl_cur;   // nlev
     uint32_t *rhist;     // 256: radix histogram
@@ -92,7 +94,7 @@ __host__ __device__ inline uint32_t q_count_words(uint32_t BR, int cw) { return 
 __host__ __device__ inline size_t qsmem_bytes(uint32_t cap, uint32_t kp, uint32_t BR, uint32_t B, int NT, uint32_t L,
                                               int cw)
 {
-    size_t b = size_t(cap) * 8 + size_t(kp) * 8 + 8 * 4 + 3 * size_t(q_nlev(L)) * 4 + 256 * 4 + NT * 4 +
+    size_t b = size_t(cap) * 8 + size_t(kp) * 8 + 8 * 4 + 2 * size_t(q_nlev(L)) * 4 + 256 * 4 + NT * 4 +
                (NT + 1) * 4 + NT * 4 + NT * 4 + (NT / 32) * 4;
     b = (b + 15) & ~size_t(15);
     b += size_t(q_count_words(BR, cw)) * 4;
@@ -108,8 +110,7 @@ __device__ inline QSmem carve_q(unsigned char *sm, uint32_t cap, uint32_t kp, ui
     s.buf = (uint64_t *)sm;
     s.keep = s.buf + cap;
     s.u = (uint32_t *)(s.keep + kp);
-    s.hist_s = s.u + 8;
-    s.lvl_n = s.hist_s + nlev;
+    s.lvl_n = s.u + 8;
     s.lvl_cur = s.lvl_n + nlev;
     s.rhist = s.lvl_cur + nlev;
     s.c_start = s.rhist + 256;
@@ -180,10 +181,10 @@ __device__ uint32_t block_excl_scan(uint32_t v, uint32_t *wsum, uint32_t *total)
     return before + x - v;
 }
 
-// Largest i in [0, n) with pre[i] <= j (pre ascending, pre[0] = 0 <= j).
-__device__ inline uint32_t find_seg(const uint32_t *pre, uint32_t n, uint32_t j)
+// Largest i in [lo, n) with pre[i] <= j (pre ascending, pre[lo] <= j).
+__device__ inline uint32_t find_seg(const uint32_t *pre, uint32_t n, uint32_t j, uint32_t lo = 0)
 {
-    uint32_t lo = 0, hi = n;
+    uint32_t hi = n;
     while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
         if (pre[mid] <= j) lo = mid;
@@ -272,6 +273,23 @@ template <int NT, int CW>
 __device__ uint64_t block_compact(const QSmem &s, uint32_t nbuf, uint32_t kk)
 {
     const int lane = threadIdx.x & 31;
+    if (nbuf <= kRankSelectMax) {
+        // few keys (the common case once the admission bound is tight): a
+        // key's rank is its count of smaller keys (keys are distinct); the
+        // kk lowest ranks land in order, and the bound is the last of them
+        for (uint32_t i = threadIdx.x; i < nbuf; i += NT) {
+            const uint64_t x = s.buf[i];
+            uint32_t r = 0;
+            for (uint32_t j = 0; j < nbuf; ++j) r += s.buf[j] < x ? 1u : 0u;
+            if (r < kk) s.keep[r] = x;
+        }
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < kk; i += NT) s.buf[i] = s.keep[i];
+        const uint64_t top = s.keep[kk - 1];
+        if (threadIdx.x == 0) s.u[0] = kk;
+        __syncthreads();
+        return top;
+    }
     uint64_t prefix, mask;
     block_select<NT, CW>(s.buf, nbuf, kk, s, prefix, mask);
     if (threadIdx.x == 0) s.u[1] = 0u;
@@ -354,12 +372,19 @@ __device__ void gather_counts(const QArgs &a, const QSmem &s, const uint32_t *qb
                 uint32_t acc[kPer];
 #pragma unroll
                 for (int j = 0; j < kPer; ++j) acc[j] = 0u;
-                for (uint32_t i = 0; i < nh; ++i) {
-                    const uint32_t x = __ldg(a.hbm + size_t(s.g_hl[i]) * a.BRw + w);
+                // eight bitmap words in flight before they are added
+                for (uint32_t i0 = 0; i0 < nh; i0 += 8) {
+                    uint32_t x[8];
 #pragma unroll
-                    for (int j = 0; j < kPer; ++j) {
-                        if constexpr (CW == 1) acc[j] += ((x >> (4 * j)) & 0xFu) * 0x00204081u & 0x01010101u;
-                        else acc[j] += ((x >> (2 * j)) & 0x3u) * 0x8001u & 0x10001u;
+                    for (int v = 0; v < 8; ++v)
+                        x[v] = i0 + v < nh ? __ldg(a.hbm + size_t(s.g_hl[i0 + v]) * a.BRw + w) : 0u;
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+#pragma unroll
+                        for (int j = 0; j < kPer; ++j) {
+                            if constexpr (CW == 1) acc[j] += ((x[v] >> (4 * j)) & 0xFu) * 0x00204081u & 0x01010101u;
+                            else acc[j] += ((x[v] >> (2 * j)) & 0x3u) * 0x8001u & 0x10001u;
+                        }
                     }
                 }
 #pragma unroll
@@ -401,7 +426,6 @@ __device__ inline void zero_query_state(const QArgs &a, const QSmem &s)
     for (uint32_t i = tid; i < nwords; i += NT) s.cntw[i] = 0u;
     const uint32_t nlev = q_nlev(a.L);
     for (uint32_t i = tid; i < nlev; i += NT) {
-        s.hist_s[i] = 0u;
         s.lvl_n[i] = 0u;
     }
     if (tid < 8) s.u[tid] = 0u;
@@ -453,13 +477,22 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
             if (v >= a.t_min) lvl_cells[atomicAdd(&s.lvl_cur[v], 1u)] = uint16_t(b);
         }
         __syncthreads();
-        // decode, level by level
+        // decode, level by level. After level t every point of score >= t has
+        // been seen (its repetition-0 cell has count >= t), so the walk stops
+        // once the kq-th best candidate scores >= t: no later point can enter.
         uint64_t bound = CountWidth<CW>::kKeyBits;   // admission: key <= bound
-        uint32_t seen = 0;                   // points with score >= current level
+        bool have_k = false;                 // kq candidates held at the last check
+        uint32_t kth_score = 0;              // score of the kq-th best candidate then
         const uint32_t sub = a.cap - a.kp;   // members per round (room after a compaction)
-        for (int t = int(a.L); t >= int(a.t_min); --t) {
-            const uint32_t nc = s.lvl_n[t];
-            const uint32_t first = s.lvl_cur[t] - nc;
+        // Levels are taken in groups: level t and the levels below it while the
+        // group holds at most a.gcells cells (about one round of members). A
+        // group's cells are contiguous in lvl_cells (levels descending).
+        int t = int(a.L);
+        while (t >= int(a.t_min)) {
+            uint32_t nc = s.lvl_n[t];
+            int t_end = t;
+            while (t_end > int(a.t_min) && nc + s.lvl_n[t_end - 1] <= a.gcells) nc += s.lvl_n[--t_end];
+            const uint32_t first = s.lvl_cur[t] - s.lvl_n[t];
             for (uint32_t c0 = 0; c0 < nc; c0 += NT) {
                 const uint32_t ci = c0 + tid;
                 uint32_t ms = 0, sz = 0, b = 0;
@@ -472,9 +505,14 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                 const uint32_t pre = block_excl_scan<NT>(sz, s.wsum, &M);
                 s.c_start[tid] = ms;
                 s.c_pre[tid] = pre;
-                s.c_cell[tid] = b;
+                s.c_cell[tid] = b | (cnt_at<CW>(s, b) << 16);   // cell and its count (its level)
                 const uint32_t ncc = min(uint32_t(NT), nc - c0);
                 __syncthreads();
+                // each (lane, u) walks member indices upwards: its cell index
+                // only moves forward, so the search starts from the last one
+                uint32_t hint[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) hint[u] = 0;
                 for (uint32_t j0 = 0; j0 < M; j0 += sub) {
                     const uint32_t jn = min(M, j0 + sub);
                     // every thread reads the buffer fill before any warp of this
@@ -495,7 +533,10 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                             in[u] = j < jn;
                             cell[u] = 0;
                             if (in[u]) {
-                                const uint32_t cs = find_seg(s.c_pre, ncc, j);
+                                uint32_t cs = hint[u];
+                                for (int step = 0; step < 4 && cs + 1 < ncc && s.c_pre[cs + 1] <= j; ++step) ++cs;
+                                if (cs + 1 < ncc && s.c_pre[cs + 1] <= j) cs = find_seg(s.c_pre, ncc, j, cs);
+                                hint[u] = cs;
                                 cell[u] = s.c_cell[cs];
                                 load_record<RW>(a.mrec, s.c_start[cs] + (j - s.c_pre[cs]), w[u]);
                             }
@@ -506,9 +547,9 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                             uint32_t score = 0xFFFFu, last = 0, x = 0;
                             if (in[u]) {
                                 x = w[u][0];
-                                // repetition 0: the cell itself, at count t
-                                score = uint32_t(t);
-                                last = cell[u];
+                                // repetition 0: the cell itself, at its level
+                                score = cell[u] >> 16;
+                                last = cell[u] & 0xFFFFu;
 #pragma unroll
                                 for (int r = 1; r < 2 * RW - 1; ++r) {
                                     if (r < int(a.R)) {
@@ -525,9 +566,6 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                                 }
                                 valid = score >= a.t_min;
                             }
-                            // points seen per score: one shared-memory atomic per distinct score per warp
-                            const uint32_t grp = __match_any_sync(0xffffffffu, valid ? score : 0xFFFFu);
-                            if (valid && lane == __ffs(grp) - 1) atomicAdd(&s.hist_s[score], __popc(grp));
                             const uint64_t key = (uint64_t(kScoreMax - score) << 48) | (uint64_t(last) << 32) | x;
                             const bool want = valid && key <= bound;
                             const uint32_t wm = __ballot_sync(0xffffffffu, want);
@@ -542,8 +580,19 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                     __syncthreads();
                 }
             }
-            seen += s.hist_s[t];             // final: later levels only add scores < t
-            if (seen >= kq) break;
+            if (nc > 0) {
+                // the buffer fill is final after the last round's barrier; the
+                // compaction's own barriers order its writes after every read
+                const uint32_t nb = s.u[0];
+                if (nb >= kq) {
+                    bound = block_compact<NT, CW>(s, nb, kq);
+                    kth_score = kScoreMax - uint32_t(bound >> 48);
+                    have_k = true;
+                }
+            }
+            // every level >= t_end is complete: points of score >= t_end are all seen
+            if (have_k && kth_score >= uint32_t(t_end)) break;
+            t = t_end - 1;
         }
     }
     __syncthreads();
