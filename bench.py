@@ -1033,7 +1033,8 @@ def run_serving(args) -> dict:
     ix2.tune(q2, 100)
     # embedding index (streamed build)
     ix4 = F.Index("cosine", c4["R"], c4["B"], c4["L"], c4["K"], capacity=c4["N"], params=c4["params"],
-                  dim=c4["d"], W=c4["W"])
+                  dim=c4["d"], W=c4["W"],
+                  precision=F.PREC_BF16X2 if args.precision == "bf16x2" else F.PREC_FP32)
     t0 = time.perf_counter()
     build_streamed(F, ix4, c4, dev, torch.from_numpy(c4["perm"].view(np.int32)).to(dev))
     torch.cuda.synchronize()
@@ -1116,7 +1117,8 @@ def run_serving(args) -> dict:
                                "in {1,10,100}; one insert batch of 1k-100k reads per run into the genomic index",
                    "form": "serving: continuous batching, 8 streams, batches <= 1024, host buffers in and out",
                    "rates": "0.25x, 0.5x, 0.9x and 2.0x (overload) of the plain form's mixed throughput",
-                   "hbm_budget_bytes": int(ix2.device_bytes + ix4.device_bytes + (4 << 30))},
+                   "hbm_budget_bytes": int(ix2.device_bytes + ix4.device_bytes + (4 << 30)),
+                   "srp_precision": "BF16x2 tcgen05" if args.precision == "bf16x2" else "FP32 FFMA"},
         "plain_form": {"mixed_qps": plain_mix, "C2_qps": plain["C2"]["qps"], "C4_qps": plain["C4"]["qps"],
                        "note": "hash kernel then count/decode/top-k kernel, whole query batch of each index "
                                "resident in HBM, per-query k uniform in {1,10,100} as served"},
