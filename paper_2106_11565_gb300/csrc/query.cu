@@ -38,10 +38,12 @@ QArgs make_args(flinng_index *ix, const uint32_t *qb, uint32_t nq)
 
 // Candidate buffer: room for one full round of members after a compaction
 // to k keys; tune->cap overrides the default when large enough.
-void pick_buffer(QArgs &a, int NT, const QueryTuning *tune, size_t extra, size_t *smem_out, int cw)
+void pick_buffer(QArgs &a, int NT, const QueryTuning *tune, size_t extra, size_t *smem_out, int cw, int unroll)
 {
     a.kp = pow2_at_least(a.k_max > 1 ? a.k_max : 2);
-    const uint32_t cap_min = pow2_at_least(a.kp + 2 * NT);
+    // the decode appends freely up to cap - (NT + 32) * unroll, then compacts:
+    // that mark must stay above the kp keys a compaction keeps
+    const uint32_t cap_min = pow2_at_least(a.kp + uint32_t(NT + 32) * unroll + 1);
     uint32_t cap = (tune && tune->cap) ? pow2_at_least(tune->cap) : 2048;
     if (cap < cap_min) cap = cap_min;
     a.cap = cap;
@@ -51,9 +53,9 @@ void pick_buffer(QArgs &a, int NT, const QueryTuning *tune, size_t extra, size_t
         smem = qsmem_bytes(a.cap, a.kp, a.BR, a.B, NT, a.L, cw);
     }
     *smem_out = smem;
-    // a level group holds about one round of members
+    // a level group holds about 4,096 members: one stop check per group
     const uint32_t per = a.avg_cell ? a.avg_cell : 1u;
-    uint32_t g = (a.cap - a.kp) / per;
+    uint32_t g = 4096u / per;
     a.gcells = g < 1 ? 1u : (g > uint32_t(NT) ? uint32_t(NT) : g);
 }
 
@@ -74,11 +76,11 @@ int query_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
     // B*R), wider CTAs keep about 1,024 threads per SM decoding
     int NT = 256;
     size_t smem;
-    pick_buffer(a, NT, nullptr, 0, &smem, cw);
+    pick_buffer(a, NT, nullptr, 0, &smem, cw, kPlainUnroll);
     const size_t fit = (228 * 1024) / (smem + 1024);
     if (fit < 4) {
         NT = fit < 2 ? 1024 : 512;
-        pick_buffer(a, NT, nullptr, 0, &smem, cw);
+        pick_buffer(a, NT, nullptr, 0, &smem, cw, kPlainUnroll);
     }
     if (smem > 227 * 1024)
         return set_error(FLINNG_ERR_INVALID_ARG,
@@ -146,7 +148,7 @@ static int fused_prepare(flinng_index *ix, const FusedQuery &fq, const uint32_t 
     }
     hash_bytes = (hash_bytes + 15) & ~size_t(15);
     size_t qbytes;
-    pick_buffer(a, NT, tune, hash_bytes, &qbytes, int(ix->cw));
+    pick_buffer(a, NT, tune, hash_bytes, &qbytes, int(ix->cw), 1);
     h.hash_off = qbytes;
     P->smem = qbytes + hash_bytes;
     if (P->smem > 227 * 1024)

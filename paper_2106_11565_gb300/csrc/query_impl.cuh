@@ -481,12 +481,12 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
         // been seen (its repetition-0 cell has count >= t), so the walk stops
         // once the kq-th best candidate scores >= t: no later point can enter.
         uint64_t bound = CountWidth<CW>::kKeyBits;   // admission: key <= bound
+        uint32_t bscore = 0;                 // the bound's score: lower scores cannot enter
         bool have_k = false;                 // kq candidates held at the last check
         uint32_t kth_score = 0;              // score of the kq-th best candidate then
-        const uint32_t sub = a.cap - a.kp;   // members per round (room after a compaction)
         // Levels are taken in groups: level t and the levels below it while the
-        // group holds at most a.gcells cells (about one round of members). A
-        // group's cells are contiguous in lvl_cells (levels descending).
+        // group holds at most a.gcells cells (about 4,096 members). A group's
+        // cells are contiguous in lvl_cells (levels descending).
         int t = int(a.L);
         while (t >= int(a.t_min)) {
             uint32_t nc = s.lvl_n[t];
@@ -513,24 +513,28 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                 uint32_t hint[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) hint[u] = 0;
-                for (uint32_t j0 = 0; j0 < M; j0 += sub) {
-                    const uint32_t jn = min(M, j0 + sub);
-                    // every thread reads the buffer fill before any warp of this
-                    // round adds to it, so the compaction decision is uniform
-                    const uint32_t nb0 = s.u[0];
-                    __syncthreads();
-                    if (nb0 + (jn - j0) > a.cap) bound = block_compact<NT, CW>(s, nb0, kq);
-                    // warp-uniform trip count: every lane of a warp runs every
-                    // iteration; U member records per lane are loaded before
-                    // any is decoded, so U loads are in flight per thread
-                    for (uint32_t jb = j0 + (tid & ~31u); jb < jn; jb += NT * U) {
+                // Members are decoded without per-round reservations: warps append
+                // freely while the buffer fill stays at or below hwm. A warp that
+                // sees it above hwm pauses; once every warp has paused or finished,
+                // the block compacts and the warps resume from their own cursors.
+                // Once the fill passes hwm every warp appends at most once more
+                // (its iteration in flight, 32 U keys), so the buffer cannot
+                // overflow: hwm = cap - (NT + 32) U.
+                const uint32_t hwm = a.cap - uint32_t(NT + 32) * U;
+                uint32_t jb = tid & ~31u;         // this warp's cursor (warp-uniform)
+                for (;;) {
+                    while (jb < M) {
+                        // the fill, read once per warp (lane 0) so the decision is warp-uniform
+                        uint32_t fill = lane == 0 ? *reinterpret_cast<volatile uint32_t *>(&s.u[0]) : 0u;
+                        fill = __shfl_sync(0xffffffffu, fill, 0);
+                        if (fill > hwm) break;
                         uint32_t w[U][RW];
                         uint32_t cell[U];
                         bool in[U];
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
                             const uint32_t j = jb + uint32_t(u) * NT + lane;
-                            in[u] = j < jn;
+                            in[u] = j < M;
                             cell[u] = 0;
                             if (in[u]) {
                                 uint32_t cs = hint[u];
@@ -552,22 +556,24 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                                 last = cell[u] & 0xFFFFu;
 #pragma unroll
                                 for (int r = 1; r < 2 * RW - 1; ++r) {
-                                    if (r < int(a.R)) {
-                                        const uint32_t g = (w[u][1 + (r - 1) / 2] >> (16 * ((r - 1) & 1))) & 0xFFFFu;
-                                        const uint32_t c = uint32_t(r) * a.B + g;
-                                        const uint32_t v = cnt_at<CW>(s, c);
-                                        if (v < score) {
-                                            score = v;
-                                            last = c;
-                                        } else if (v == score) {
-                                            last = c;
-                                        }
+                                    if (r >= int(a.R)) break;
+                                    const uint32_t g = (w[u][1 + (r - 1) / 2] >> (16 * ((r - 1) & 1))) & 0xFFFFu;
+                                    const uint32_t c = uint32_t(r) * a.B + g;
+                                    const uint32_t v = cnt_at<CW>(s, c);
+                                    if (v <= score) {
+                                        last = c;
+                                        score = v;
                                     }
                                 }
-                                valid = score >= a.t_min;
+                                // a score below the bound's cannot enter: skip the 64-bit key
+                                valid = score >= a.t_min && score >= bscore;
                             }
-                            const uint64_t key = (uint64_t(kScoreMax - score) << 48) | (uint64_t(last) << 32) | x;
-                            const bool want = valid && key <= bound;
+                            uint64_t key = 0;
+                            bool want = false;
+                            if (valid) {
+                                key = (uint64_t(kScoreMax - score) << 48) | (uint64_t(last) << 32) | x;
+                                want = key <= bound;
+                            }
                             const uint32_t wm = __ballot_sync(0xffffffffu, want);
                             if (wm) {
                                 uint32_t base = 0;
@@ -576,8 +582,13 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                                 if (want) s.buf[base + __popc(wm & ((1u << lane) - 1u))] = key;
                             }
                         }
+                        jb += NT * U;
                     }
                     __syncthreads();
+                    const uint32_t nb0 = s.u[0];   // same value in every thread (read after the barrier)
+                    if (nb0 <= hwm) break;          // no warp paused: every cursor is at its end
+                    bound = block_compact<NT, CW>(s, nb0, kq);
+                    bscore = kScoreMax - uint32_t(bound >> 48);
                 }
             }
             if (nc > 0) {
@@ -587,6 +598,7 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                 if (nb >= kq) {
                     bound = block_compact<NT, CW>(s, nb, kq);
                     kth_score = kScoreMax - uint32_t(bound >> 48);
+                    bscore = kth_score;
                     have_k = true;
                 }
             }
