@@ -681,6 +681,23 @@ def time_oracle_queries(o, c: dict, target_s: float = 10.0, max_rounds: int = 10
 # main arm
 # --------------------------------------------------------------------------
 
+def max_over_ranks(v: float, dist, device) -> float:
+    """The largest v over all ranks, returned on every rank (v itself when
+    there is no process group)."""
+    if dist is None:
+        return float(v)
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, world: int, slowest_s: float) -> float:
+    """Whole-job throughput of N independent replicas: all ranks' units over
+    the slowest rank's time."""
+    return world * units_per_rank / slowest_s
+
+
 def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     import torch
     from paper_2106_11565_gb300 import _build
@@ -801,13 +818,9 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     if dist is not None:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * nq * args.steps / (total_ms / 1e3)
+    value = replica_throughput(nq * args.steps, world, total_ms / 1e3)
 
     # ---- the plain form, same batch, per-stage events
     for it in range(args.warmup):
@@ -828,7 +841,7 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     hash_ms = [a.elapsed_time(m) for a, m, _ in pev]
     query_ms = [m.elapsed_time(b) for _, m, b in pev]
     plain_ms = [a.elapsed_time(b) for a, _, b in pev]
-    plain_value = world * nq / (statistics.mean(plain_ms) / 1e3)
+    plain_value = replica_throughput(nq, world, statistics.mean(plain_ms) / 1e3)
 
     # ---- e2e: flinng_query with host (pinned) buffers, copies inside the call
     if c.get("embed"):
@@ -851,13 +864,9 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
         t0 = time.perf_counter()
         h_ids, h_sc = ix.query(h_q, k)
         e2e_s.append(time.perf_counter() - t0)
-    e2e_total = float(sum(e2e_s))
-    if dist is not None:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * nq * args.steps / e2e_total
-    d2h = nq * k * 5
+    e2e_total = max_over_ranks(sum(e2e_s), dist, dev)
+    e2e_value = replica_throughput(nq * args.steps, world, e2e_total)
+    d2h = nq * k * 6                                 # uint32 ids + uint16 scores
 
     # ---- serving form on this index: Poisson traces through the C runtime
     serving = None
