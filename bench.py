@@ -25,6 +25,7 @@ import argparse
 import ctypes as C
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -681,6 +682,30 @@ def time_oracle_queries(o, c: dict, target_s: float = 10.0, max_rounds: int = 10
 # main arm
 # --------------------------------------------------------------------------
 
+def advisor_section(c: dict, ex_sims, kk: int = 10) -> dict:
+    """Thm. 3's design and the gamma-stability of the sampled queries, from
+    their exact k-th and (k+1)-th neighbour similarities (host arithmetic)."""
+    from paper_2106_11565_gb300 import advisor as A
+    sims = np.asarray(ex_sims, dtype=np.float64)
+    sk, sk1 = sims[:, kk - 1], sims[:, kk]
+    ok = (sk1 > 0) & (sk1 < sk) & (sk <= 1)
+    if not ok.any():
+        return {"note": f"no sampled query has 0 < s_{kk + 1} < s_{kk} <= 1"}
+    gam = np.array([A.gamma(a, b) for a, b in zip(sk[ok], sk1[ok])])
+    d = A.design(c["N"], float(np.median(sk[ok])), float(np.median(sk1[ok])), 0.99, 0.01)
+    return {"k": kk, "queries": int(ok.sum()),
+            "gamma": {"p10": float(np.percentile(gam, 10)), "p50": float(np.median(gam)),
+                      "p90": float(np.percentile(gam, 90))},
+            "median_s_k": float(np.median(sk[ok])), "median_s_k_plus_1": float(np.median(sk1[ok])),
+            "theory_design": {"B": d["B"], "K": d["K"], "log10_L": d["log10_L"], "alpha": d["alpha"],
+                              "L": d["L"] if d["log10_L"] < 15 else None,
+                              "t": d["t"] if d["log10_L"] < 15 else None},
+            "configured": {"R": c["R"], "B": c["B"], "L": c["L"], "K": c["K"]},
+            "note": "Thm. 3 for p' = 0.99, q' = 0.01 at the median gap (library names: L tables = the "
+                    "paper's m, K bits = the paper's L); large gamma means a query whose neighbours are "
+                    "hard to separate, for which the theory asks for many tables"}
+
+
 def max_over_ranks(v: float, dist, device) -> float:
     """The largest v over all ranks, returned on every rank (v itself when
     there is no process group)."""
@@ -885,6 +910,7 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
         smp = gt_sample(c)
         rec = recall_scores(c, out_ids[smp], ex_ids, ex_sims)
         rec["queries"] = int(len(smp))
+        rec["advisor"] = advisor_section(c, ex_sims)
     sweep = None
     if not args.no_recall and not args.no_sweep and args.workload in SWEEPS:
         sweep = recall_sweep(F, c, args.workload, prec, dev, d_pts, d_q, ex_ids, ex_sims, smp, flush,
