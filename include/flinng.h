@@ -235,6 +235,23 @@ int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq,
                   uint16_t *out_counts, int on_device);
 
 /*
+ * Query from per-cell counts instead of query buckets: Alg. 3's group tests,
+ * AND-over-R decode and top-k on counts the caller supplies (Sec. 5: the
+ * count of a cell is the number of tables whose list for the query's bucket
+ * holds it). This is the decode step of a table-sharded index: each shard
+ * holds a disjoint subset of the tables over the same groups (same points and
+ * permutation), flinng_counts gives its partial counts, their sum over shards
+ * (an all-reduce) equals the counts of the whole index, and this call decodes
+ * them on any one shard.
+ * counts: nq x (B*R) uint16. max_count: the total number of tables (the
+ * largest count possible, 1..4095); larger values are clamped to it.
+ * Same k, k_max and outputs as flinng_query. Errors: INVALID_ARG, CUDA.
+ */
+int flinng_query_counts(flinng_index *idx, const uint16_t *counts, uint32_t nq,
+                        uint32_t max_count, const uint32_t *k, uint32_t k_max,
+                        uint32_t *out_ids, uint16_t *out_scores, int on_device);
+
+/*
  * Copy the index out to HOST buffers (synchronous).
  * off: L * 2^W + 1 uint32 CSR offsets; cells: the cell lists (cells_cap
  * entries available; *n_cells receives the count); gid: size x R uint16

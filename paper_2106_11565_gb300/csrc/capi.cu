@@ -601,6 +601,46 @@ int flinng_query_buckets(flinng_index *idx, const uint32_t *qbuckets, uint32_t n
     return query_common(idx, nullptr, qbuckets, nq, k, k_max, out_ids, out_scores, on_device);
 }
 
+int flinng_query_counts(flinng_index *idx, const uint16_t *counts, uint32_t nq, uint32_t max_count,
+                        const uint32_t *k, uint32_t k_max, uint32_t *out_ids, uint16_t *out_scores, int on_device)
+{
+    if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
+    if (k_max > kMaxKMax) return set_error(FLINNG_ERR_INVALID_ARG, "query_counts: k_max > %u", kMaxKMax);
+    if (max_count < 1 || max_count > kMaxL)
+        return set_error(FLINNG_ERR_INVALID_ARG, "query_counts: max_count must be in 1..%u", kMaxL);
+    if (nq == 0) return FLINNG_OK;
+    if (!counts || !out_ids) return set_error(FLINNG_ERR_INVALID_ARG, "query_counts: null counts or out_ids");
+    if (k && !on_device)
+        for (uint32_t i = 0; i < nq; ++i)
+            if (k[i] > k_max) return set_error(FLINNG_ERR_INVALID_ARG, "query_counts: k[%u] = %u > k_max", i, k[i]);
+    if (on_device)
+        return query_launch_counts(idx, nullptr, counts, max_count, nq, k, k_max, out_ids, out_scores);
+    const cudaStream_t st = idx->stream;
+    const uint64_t BR = idx->BR;
+    FL_TRY(ws_reserve(idx, 4096 + carve_bytes<uint16_t>(nq * BR) + carve_bytes<uint32_t>(nq) +
+                               carve_bytes<uint32_t>(uint64_t(nq) * k_max) + carve_bytes<uint16_t>(uint64_t(nq) * k_max)));
+    Carver c(idx->ws.ptr, idx->ws.bytes);
+    uint16_t *dc = c.take<uint16_t>(nq * BR);
+    FL_CUDA(cudaMemcpyAsync(dc, counts, nq * BR * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
+    const uint32_t *dk = nullptr;
+    if (k) {
+        uint32_t *t = c.take<uint32_t>(nq);
+        FL_CUDA(cudaMemcpyAsync(t, k, nq * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+        dk = t;
+    }
+    uint32_t *dids = c.take<uint32_t>(uint64_t(nq) * k_max);
+    uint16_t *dsc = out_scores ? c.take<uint16_t>(uint64_t(nq) * k_max) : nullptr;
+    FL_TRY(query_launch_counts(idx, nullptr, dc, max_count, nq, dk, k_max, dids, dsc));
+    if (k_max) {
+        FL_CUDA(cudaMemcpyAsync(out_ids, dids, uint64_t(nq) * k_max * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        if (out_scores)
+            FL_CUDA(cudaMemcpyAsync(out_scores, dsc, uint64_t(nq) * k_max * sizeof(uint16_t),
+                                    cudaMemcpyDeviceToHost, st));
+    }
+    FL_CUDA(cudaStreamSynchronize(st));
+    return FLINNG_OK;
+}
+
 int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq, uint16_t *out_counts,
                   int on_device)
 {

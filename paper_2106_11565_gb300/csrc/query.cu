@@ -65,9 +65,21 @@ int query_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
                  const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
                  uint16_t *out_scores)
 {
+    return query_launch_counts(ix, qbuckets, nullptr, 0, nq, k, k_max, out_ids, out_scores);
+}
+
+int query_launch_counts(flinng_index *ix, const uint32_t *qbuckets, const uint16_t *counts, uint32_t max_count,
+                        uint32_t nq, const uint32_t *k, uint32_t k_max, uint32_t *out_ids, uint16_t *out_scores)
+{
     if (nq == 0) return FLINNG_OK;
     QArgs a = make_args(ix, qbuckets, nq);
-    const int cw = int(ix->cw);
+    int cw = int(ix->cw);
+    if (counts) {
+        // decode from given counts: levels run to the caller's table total
+        a.cnt_in = counts;
+        a.L = max_count;
+        cw = max_count <= 255 ? 1 : 2;
+    }
     a.k = k;
     a.k_max = k_max;
     a.out_ids = out_ids;

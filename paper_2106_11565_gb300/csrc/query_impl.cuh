@@ -52,6 +52,7 @@ template <> struct CountWidth<2> {
 
 struct QArgs {
     const uint32_t *qb;
+    const uint16_t *cnt_in;   // per-cell counts given by the caller (nq x BR), or null: gather them
     uint32_t nq;
     const uint32_t *k;
     uint32_t k_max;
@@ -418,6 +419,27 @@ __device__ void gather_counts(const QArgs &a, const QSmem &s, const uint32_t *qb
     }
 }
 
+// Per-cell counts given by the caller (e.g. the sum of table shards' counts)
+// packed into the shared counters; values above L (here the caller's total
+// table count) are clamped to L. Contains __syncthreads.
+template <int NT, int CW>
+__device__ void load_counts(const QArgs &a, const QSmem &s, const uint16_t *cnt)
+{
+    constexpr uint32_t kPer = CW == 1 ? 4u : 2u;
+    const uint32_t nwords = q_count_words(a.BR, CW);
+    for (uint32_t i = threadIdx.x; i < nwords; i += NT) {
+        uint32_t wv = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < kPer; ++j) {
+            const uint32_t c = i * kPer + j;
+            const uint32_t v = c < a.BR ? min(uint32_t(cnt[c]), a.L) : 0u;
+            wv |= v << (j * (CW == 1 ? 8u : 16u));
+        }
+        s.cntw[i] = wv;
+    }
+    __syncthreads();
+}
+
 template <int NT, int CW>
 __device__ inline void zero_query_state(const QArgs &a, const QSmem &s)
 {
@@ -663,7 +685,10 @@ k_query(QArgs a)
         if (kq > a.k_max) kq = a.k_max;
         zero_query_state<NT, CW>(a, s);
         __syncthreads();
-        if (kq > 0) gather_counts<NT, CW, kPlainUnroll>(a, s, a.qb + size_t(q) * a.L);
+        if (kq > 0) {
+            if (a.cnt_in) load_counts<NT, CW>(a, s, a.cnt_in + size_t(q) * a.BR);
+            else gather_counts<NT, CW, kPlainUnroll>(a, s, a.qb + size_t(q) * a.L);
+        }
         decode_topk<NT, RW, CW, kPlainUnroll>(a, s, q, kq);
     }
 }

@@ -94,6 +94,8 @@ _SIGS = {
                                 C.POINTER(C.c_uint64), C.c_void_p]),
     "flinng_hash_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "flinng_hash_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    "flinng_query_counts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_uint32,
+                                      C.c_void_p, C.c_void_p, C.c_int]),
     "flinng_kernel_launches": (C.c_uint64, []),
     "flinng_set_query_mode": (C.c_int, [C.c_void_p, C.c_uint32]),
     "flinng_tune_query": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint32, C.c_uint32,
@@ -308,6 +310,19 @@ class Index:
         kk = None if k is None else (k if _is_cuda(k) else _np(k, np.uint32))
         _check(self.lib.flinng_query_buckets(self.h, _ptr(qb), nq, _ptr(kk), k_max, _ptr(ids),
                                              _ptr(sc), dev))
+        return ids, sc
+
+    def query_counts(self, counts, k_max: int, max_count: int, k=None):
+        """Decode from per-cell counts (nq x B*R, e.g. summed over table
+        shards); max_count is the total table count."""
+        dev = int(_is_cuda(counts))
+        counts = counts if dev else _np(counts, np.uint16)
+        nq = counts.shape[0]
+        ids = self._out(dev, (nq, k_max), np.uint32)
+        sc = self._out(dev, (nq, k_max), np.uint16)
+        kk = None if k is None else (k if _is_cuda(k) else _np(k, np.uint32))
+        _check(self.lib.flinng_query_counts(self.h, _ptr(counts), nq, max_count, _ptr(kk), k_max, _ptr(ids),
+                                            _ptr(sc), dev))
         return ids, sc
 
     def counts(self, qb):
