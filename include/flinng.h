@@ -163,6 +163,25 @@ int flinng_query(flinng_index *idx, const flinng_points *q, uint32_t nq,
 /* Destroy the index and free its device memory. NULL is a no-op. */
 int flinng_destroy(flinng_index *idx);
 
+/*
+ * Save a built index to a file, and load it back onto the current device
+ * (the index of Sec. 5 with its groups from Alg. 1). The file holds the
+ * configuration, the hash parameters, the group ids, member lists and
+ * records, each table's bucket-to-cell lists and the heavy buckets' cell
+ * bitmaps. A loaded index answers every query exactly as the saved one
+ * and takes inserts up to the same capacity. The format is this library's
+ * own (little endian, versioned); it is not portable across byte orders.
+ * flinng_save synchronises the index's stream; flinng_load allocates like
+ * flinng_create and runs on `stream`.
+ * Errors: INVALID_ARG (unreadable, wrong or truncated file; a file that
+ * exceeds its stated capacity), OOM, CUDA.
+ */
+int flinng_save(flinng_index *idx, const char *path);
+int flinng_load(const char *path, void *stream, flinng_index **out);
+
+/* The configuration an index was created (or loaded) with. */
+int flinng_get_config(const flinng_index *idx, flinng_config *out);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *flinng_last_error(void);
 

@@ -94,6 +94,9 @@ _SIGS = {
                                 C.POINTER(C.c_uint64), C.c_void_p]),
     "flinng_hash_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "flinng_hash_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    "flinng_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "flinng_load": (C.c_int, [C.c_char_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "flinng_get_config": (C.c_int, [C.c_void_p, C.c_void_p]),
     "flinng_query_counts": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_uint32,
                                       C.c_void_p, C.c_void_p, C.c_int]),
     "flinng_kernel_launches": (C.c_uint64, []),
@@ -219,6 +222,30 @@ class Index:
         h = C.c_void_p()
         _check(self.lib.flinng_create(C.byref(self.cfg), C.byref(p), C.c_void_p(stream), C.byref(h)))
         self.h = h
+
+    # ---- persistence
+    def save(self, path: str):
+        """Write the built index to a file (flinng_save)."""
+        _check(self.lib.flinng_save(self.h, str(path).encode()))
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Index":
+        """An index read back from a file written by save (flinng_load)."""
+        obj = cls.__new__(cls)
+        obj.lib = load()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        obj.stream = stream
+        h = C.c_void_p()
+        _check(obj.lib.flinng_load(str(path).encode(), C.c_void_p(stream), C.byref(h)))
+        obj.h = h
+        obj.cfg = flinng_config()
+        _check(obj.lib.flinng_get_config(h, C.byref(obj.cfg)))
+        c = obj.cfg
+        obj.metric = "cosine" if c.metric == COSINE_SRP else "jaccard"
+        obj.R, obj.B, obj.L, obj.K, obj.W = c.R, c.B, c.L, c.K, c.range_bits
+        return obj
 
     # ---- lifecycle
     def close(self):
