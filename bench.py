@@ -458,6 +458,7 @@ def serving_runs(F, ix, c: dict, plain_qps: float, factors, check_sample: int = 
     srv = F.Server(hbm_budget=ix.device_bytes + (2 << 30), n_slots=8, max_batch=1024, k_max=k,
                    max_batch_elems=1 << 21)
     sid = srv.add_index(ix)
+    staging = srv.staging
     src = (sets_source(F, sid, c["q"], 1.0, keep) if c["metric"] != "cosine"
            else dense_source(F, sid, torch.from_numpy(c["q"]).pin_memory().numpy(), 1.0, keep))
     rng_t = np.random.default_rng([c["seed"], 77])
@@ -488,6 +489,7 @@ def serving_runs(F, ix, c: dict, plain_qps: float, factors, check_sample: int = 
             same = {"checked": int(len(pick)), "equal": ok}
     srv.close()
     out = {"form": "continuous batching (C runtime, 8 streams, batches <= 1024, host buffers)",
+           "staging": staging,
            "plain_form_qps": plain_qps, "runs": runs,
            "max_qps": max(r["achieved_qps"] for r in runs.values()),
            "note": "offered load relative to the plain form's device-resident throughput; the serving "
@@ -1102,6 +1104,7 @@ def run_serving(args) -> dict:
                    k_max=100, max_batch_elems=1 << 21)
     id2 = srv.add_index(ix2)
     id4 = srv.add_index(ix4)
+    staging5 = srv.staging
     h_q4 = q4.cpu().pin_memory().numpy()
     sources = [sets_source(F, id2, c2["q"], 0.5, keep), dense_source(F, id4, h_q4, 0.5, keep)]
     rng = np.random.default_rng([c2["seed"], 55])
@@ -1159,6 +1162,7 @@ def run_serving(args) -> dict:
                                "resident in HBM, per-query k uniform in {1,10,100} as served"},
         "serving": runs,
         "serving_vs_plain": peak / plain_mix,
+        "staging": staging5,
         "latency_ms": {"p50_at_0.9x": runs["0.9x_plain"]["p50_ms"], "p99_at_0.9x": runs["0.9x_plain"]["p99_ms"]},
         "e2e": {"value": peak, "unit": UNIT, "h2d_bytes_per_step": int(h2d_per_q),
                 "d2h_bytes_per_step": 500, "note": "serving is host-to-host: per query bytes"},

@@ -56,7 +56,10 @@ extern "C" {
 #define FLINNG_PREC_FP32 0     /* fp32 FMA tiles; fp64 / exact re-check below a rigorous margin */
 #define FLINNG_PREC_BF16X2 1   /* tensor cores (tcgen05): each operand split into two bf16 parts,
                                   fp32 accumulation; compensated fp32, then fp64 / exact re-check of
-                                  projections below a rigorous margin; needs dim % 8 == 0 */
+                                  projections below a rigorous margin; needs dim % 8 == 0. Its
+                                  pipeline waits are bounded: a wait that gave up (never expected)
+                                  makes the index's next hash or query, and flinng_hash_counters,
+                                  return FLINNG_ERR_TIMEOUT from then on */
 
 typedef struct flinng_config {
     uint32_t metric;        /* FLINNG_COSINE_SRP or FLINNG_JACCARD_DOPH */
@@ -391,6 +394,12 @@ int flinng_server_add_index(flinng_server *srv, flinng_index *idx, uint32_t *ind
 
 /* Device bytes held by the registered indices and the slots. */
 uint64_t flinng_server_device_bytes(const flinng_server *srv);
+
+/* How the server stages query inputs: 1 = a kernel gathers them straight
+ * from the requests' host buffers (the device can read pageable host
+ * memory), 0 = the host copies them into pinned staging first. Negative:
+ * an error code (NULL server). */
+int flinng_server_staging(const flinng_server *srv);
 
 /* Serve n requests, each admitted when the clock reaches its arrival time;
  * returns when all are done. out_ids / out_scores: n x k_max (HOST), rows of

@@ -315,6 +315,7 @@ int flinng_create(const flinng_config *cfg, const flinng_params *params, void *s
     if (rc == FLINNG_OK) {
         cudaError_t e = cudaMallocHost((void **)&ix->h_flag, 16);
         if (e != cudaSuccess) rc = cuda_error(e, "cudaMallocHost");
+        else std::memset(ix->h_flag, 0, 16);
     }
     const cudaStream_t st = ix->stream;
     auto chk = [&](cudaError_t e, const char *w) {
@@ -342,6 +343,7 @@ int flinng_create(const flinng_config *cfg, const flinng_params *params, void *s
         chk(cudaMemsetAsync(ix->hidx, 0xFF, (ix->nslot + 1) * sizeof(uint32_t), st), "clear hidx");
         chk(cudaMemsetAsync(ix->moff, 0, (size_t(ix->BR) + 1) * sizeof(uint32_t), st), "zero moff");
         chk(cudaMemsetAsync(ix->stats, 0, kStats * sizeof(unsigned long long), st), "zero stats");
+        chk(cudaMemsetAsync(ix->tc_err, 0, 4, st), "zero tensor-core flag");
         if (rc == FLINNG_OK && cfg->precision == FLINNG_PREC_BF16X2) rc = srp_tc_prepare_weights(ix);
         chk(cudaStreamSynchronize(st), "create sync");
     }
@@ -704,6 +706,8 @@ int flinng_hash_counters(const flinng_index *idx, uint64_t *out)
     FL_CUDA(cudaStreamSynchronize(idx->stream));
     FL_CUDA(cudaMemcpy(h, idx->stats, sizeof h, cudaMemcpyDeviceToHost));
     for (int i = 0; i < kStats; ++i) out[i] = h[i];
+    if (idx->h_flag && idx->h_flag[3])
+        return set_error(FLINNG_ERR_TIMEOUT, "tensor-core SRP: a pipeline wait timed out");
     return FLINNG_OK;
 }
 

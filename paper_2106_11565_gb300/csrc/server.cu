@@ -14,6 +14,11 @@
 // Admission is by HBM budget: an index is accepted only if its device
 // memory plus the slots' scratch fits, an insert only if the index has
 // capacity left and stays within the budget.
+// Staging: where the GPU can read any host memory (pageable memory access,
+// e.g. over NVLink-C2C on Grace systems), a batch's inputs are gathered by a
+// kernel straight from the requests' own buffers, and the host only writes a
+// small descriptor per request. Elsewhere the host copies the inputs into
+// pinned staging first.
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -49,8 +54,25 @@ struct ServerIndex {
 // Per-slot layout (device and host mirror): counter + stats, per-query k,
 // query input (rows or CSR), query buckets, re-check list, outputs.
 struct Layout {
-    size_t k, in_off, in_el, qb, srp, ids, sc, total;
+    size_t k, in_off, in_el, qb, srp, ids, sc, desc, total;
 };
+
+// One request's input for the device gather: 4-byte words from a host
+// address to a word offset of the batch's input.
+struct GatherDesc {
+    uint64_t src;
+    uint64_t dst;
+    uint64_t n;
+};
+
+__global__ void k_gather_requests(const GatherDesc *__restrict__ desc, uint32_t nb, uint32_t *__restrict__ dst)
+{
+    for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+        const GatherDesc g = desc[i];
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(g.src);
+        for (uint64_t t = threadIdx.x; t < g.n; t += blockDim.x) dst[g.dst + t] = src[t];
+    }
+}
 
 }  // namespace
 }  // namespace flinng
@@ -63,6 +85,7 @@ struct flinng_server {
     // sizes the slots are laid out for (maximum over the indices)
     uint32_t max_L = 0, max_dim = 0;
     uint64_t max_P = 0;
+    bool device_gather = false;   // the GPU reads requests' host buffers directly
 };
 
 namespace flinng {
@@ -90,6 +113,7 @@ Layout layout_for(const flinng_server *srv)
     L.srp = (size_t)c.take<unsigned long long>(2 * nb * srv->max_P + 64 + nb * srv->max_dim / 2 + nb + 1024);
     L.ids = (size_t)c.take<uint32_t>(nb * km);
     L.sc = (size_t)c.take<uint16_t>(nb * km);
+    L.desc = (size_t)c.take<GatherDesc>(nb);
     L.total = c.used + 256;
     return L;
 }
@@ -126,7 +150,30 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
     char *d = static_cast<char *>(slot.dscratch);
     uint32_t *hk = reinterpret_cast<uint32_t *>(h + Lo.k);
     size_t in_bytes;
-    if (srp) {
+    if (srv->device_gather) {
+        // descriptors only: the gather kernel reads each request's buffer
+        GatherDesc *hd = reinterpret_cast<GatherDesc *>(h + Lo.desc);
+        uint64_t *ho = reinterpret_cast<uint64_t *>(h + Lo.in_off);
+        ho[0] = 0;
+        for (uint32_t i = 0; i < nb; ++i) {
+            const flinng_request &r = reqs[slot.reqs[i]];
+            hk[i] = r.k;
+            const uint64_t n = srp ? uint64_t(ix->cfg.dim) : r.n;
+            hd[i] = GatherDesc{reinterpret_cast<uint64_t>(r.data), ho[i], r.data ? n : 0};
+            ho[i + 1] = ho[i] + n;
+        }
+        FL_CUDA(cudaMemcpyAsync(d + Lo.k, h + Lo.k, nb * sizeof(uint32_t), cudaMemcpyHostToDevice, slot.stream));
+        if (!srp)
+            FL_CUDA(cudaMemcpyAsync(d + Lo.in_off, h + Lo.in_off, (nb + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                                    slot.stream));
+        FL_CUDA(cudaMemcpyAsync(d + Lo.desc, h + Lo.desc, nb * sizeof(GatherDesc), cudaMemcpyHostToDevice,
+                                slot.stream));
+        const unsigned grid = nb < 152u * 8u ? nb : 152u * 8u;
+        k_gather_requests<<<grid, 256, 0, slot.stream>>>(reinterpret_cast<const GatherDesc *>(d + Lo.desc), nb,
+                                                          reinterpret_cast<uint32_t *>(d + Lo.in_el));
+        count_launch();
+        FL_CUDA(cudaGetLastError());
+    } else if (srp) {
         float *hx = reinterpret_cast<float *>(h + Lo.in_el);
         for (uint32_t i = 0; i < nb; ++i) {
             const flinng_request &r = reqs[slot.reqs[i]];
@@ -206,6 +253,12 @@ int flinng_server_create(const flinng_server_config *cfg, flinng_server **out)
                          kMaxKMax);
     flinng_server *srv = new flinng_server();
     srv->cfg = *cfg;
+    {
+        int dev = 0, pageable = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) == cudaSuccess)
+            srv->device_gather = pageable != 0;
+    }
     srv->slots.resize(cfg->n_slots);
     for (Slot &s : srv->slots) {
         cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
@@ -401,3 +454,12 @@ int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_
 }
 
 }  // extern "C"
+
+extern "C" int flinng_server_staging(const flinng_server *srv)
+{
+    if (!srv) {
+        set_error(FLINNG_ERR_INVALID_ARG, "server: null argument");
+        return -FLINNG_ERR_INVALID_ARG;
+    }
+    return srv->device_gather ? 1 : 0;
+}

@@ -526,6 +526,8 @@ size_t srp_tc_workspace_bytes(const flinng_index *ix, uint64_t n)
 int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint32_t *buckets, float *proj,
                 void *ws)
 {
+    // a wait that timed out in an earlier call (the flag is sticky on the device)
+    if (ix->h_flag[3]) return set_error(FLINNG_ERR_TIMEOUT, "tensor-core SRP: a pipeline wait timed out");
     const cudaStream_t st = ix->stream;
     const uint32_t L = ix->cfg.L, K = ix->cfg.K, d = ix->cfg.dim, P = ix->P;
     const uint64_t chunk = kTcChunkRows;
@@ -539,7 +541,6 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
     FL_CUDA(cudaMemsetAsync(ix->stats, 0, kStats * sizeof(unsigned long long), st));
     if (n == 0) return FLINNG_OK;
     FL_CUDA(cudaMemsetAsync(buckets, 0, n * L * sizeof(uint32_t), st));
-    FL_CUDA(cudaMemsetAsync(ix->tc_err, 0, 4, st));
     const __nv_bfloat16 *w1 = static_cast<const __nv_bfloat16 *>(ix->w_split);
     CUtensorMap mw1, mw2;
     FL_TRY(make_map(&mw1, w1, P, d));
@@ -596,9 +597,9 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
         FL_TRY(srp_recheck_list(ix, x + r0 * ld, ld, list2, cnt + 1, buckets + r0 * L));
         FL_TRY(add_counter(ix->stats, cnt, st));            // undecided after the tensor-core pass
     }
-    FL_CUDA(cudaMemcpyAsync(ix->h_flag, ix->tc_err, 4, cudaMemcpyDeviceToHost, st));
-    FL_CUDA(cudaStreamSynchronize(st));
-    if (*ix->h_flag) return set_error(FLINNG_ERR_TIMEOUT, "tensor-core SRP: a pipeline wait timed out");
+    // no synchronisation here (servers hash on their own streams): the flag
+    // lands in pinned memory and the next call on this index reports it
+    FL_CUDA(cudaMemcpyAsync(ix->h_flag + 3, ix->tc_err, 4, cudaMemcpyDeviceToHost, st));
     return FLINNG_OK;
 }
 

@@ -94,6 +94,7 @@ _SIGS = {
                                 C.POINTER(C.c_uint64), C.c_void_p]),
     "flinng_hash_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "flinng_hash_counters": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    "flinng_server_staging": (C.c_int, [C.c_void_p]),
     "flinng_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "flinng_load": (C.c_int, [C.c_char_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     "flinng_get_config": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -429,6 +430,12 @@ class Server:
     @property
     def device_bytes(self) -> int:
         return int(self.lib.flinng_server_device_bytes(self.h))
+
+    @property
+    def staging(self) -> str:
+        """'device gather' (a kernel reads the requests' host buffers) or
+        'host copy' (inputs copied into pinned staging first)."""
+        return "device gather" if self.lib.flinng_server_staging(self.h) == 1 else "host copy"
 
     def replay(self, reqs):
         """reqs: a ctypes array of flinng_request or a numpy array of
