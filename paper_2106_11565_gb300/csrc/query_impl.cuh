@@ -335,10 +335,18 @@ __device__ uint64_t block_compact(const QSmem &s, uint32_t nbuf, uint32_t kk)
     return bound;
 }
 
+// Carry-save adder on 32 bit lanes: a + b + c = sum + 2 carry in every lane.
+__device__ __forceinline__ void csa(uint32_t &carry, uint32_t &sum, uint32_t a, uint32_t b, uint32_t c)
+{
+    const uint32_t u = a ^ b;
+    sum = u ^ c;
+    carry = (a & b) | (u & c);
+}
+
 // Per-cell collision counts of one query (Sec. 5), NT tables at a time.
 // Tables whose bucket is heavy contribute their cell bitmap: each thread owns
-// whole counter words and adds 4 bits (CW = 1) or 2 bits (CW = 2) at a time,
-// spread to the counters of the word by one multiply, without atomics. The
+// one bitmap word position (32 cells) and sums it over the heavy tables in
+// bit-sliced form, then adds the sums to its counter words without atomics. The
 // other tables' lists are flattened over the CTA and counted with shared-memory
 // atomics, U cell loads in flight per thread. Expects s.u[5] == 0 (the heavy
 // table count, zeroed with the query state) and leaves it 0. Contains
@@ -369,28 +377,54 @@ __device__ void gather_counts(const QArgs &a, const QSmem &s, const uint32_t *qb
         const uint32_t nh = s.u[5];
         if (nh > 0) {
             constexpr int kPer = CW == 1 ? 8 : 16;        // counter words per bitmap word
+            constexpr uint32_t kCells = 32 / kPer;        // cells per counter word
+            constexpr uint32_t kSub = 248;                // tables per pass: counts below 256, 8 bit planes
             for (uint32_t w = tid; w < a.BRw; w += NT) {
-                uint32_t acc[kPer];
+                for (uint32_t i1 = 0; i1 < nh; i1 += kSub) {
+                    const uint32_t i2 = min(nh, i1 + kSub);
+                    // bit-sliced counters of the word's 32 cells: pl[p] holds bit p
+                    // of every cell's count. Eight bitmap words at a time (loaded
+                    // together) go through a carry-save adder tree into planes 0..2;
+                    // the weight-8 carry ripples into the planes above.
+                    uint32_t pl[8];
 #pragma unroll
-                for (int j = 0; j < kPer; ++j) acc[j] = 0u;
-                // eight bitmap words in flight before they are added
-                for (uint32_t i0 = 0; i0 < nh; i0 += 8) {
-                    uint32_t x[8];
+                    for (int p = 0; p < 8; ++p) pl[p] = 0u;
+                    for (uint32_t i0 = i1; i0 < i2; i0 += 8) {
+                        uint32_t x[8];
 #pragma unroll
-                    for (int v = 0; v < 8; ++v)
-                        x[v] = i0 + v < nh ? __ldg(a.hbm + size_t(s.g_hl[i0 + v]) * a.BRw + w) : 0u;
+                        for (int v = 0; v < 8; ++v)
+                            x[v] = i0 + v < i2 ? __ldg(a.hbm + size_t(s.g_hl[i0 + v]) * a.BRw + w) : 0u;
+                        uint32_t t0, t1, f0, f1, e;
+                        csa(t0, pl[0], pl[0], x[0], x[1]);
+                        csa(t1, pl[0], pl[0], x[2], x[3]);
+                        csa(f0, pl[1], pl[1], t0, t1);
+                        csa(t0, pl[0], pl[0], x[4], x[5]);
+                        csa(t1, pl[0], pl[0], x[6], x[7]);
+                        csa(f1, pl[1], pl[1], t0, t1);
+                        csa(e, pl[2], pl[2], f0, f1);
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) {
-#pragma unroll
-                        for (int j = 0; j < kPer; ++j) {
-                            if constexpr (CW == 1) acc[j] += ((x[v] >> (4 * j)) & 0xFu) * 0x00204081u & 0x01010101u;
-                            else acc[j] += ((x[v] >> (2 * j)) & 0x3u) * 0x8001u & 0x10001u;
+                        for (int p = 3; p < 8; ++p) {
+                            const uint32_t c = pl[p] & e;
+                            pl[p] ^= e;
+                            e = c;
                         }
                     }
-                }
+                    // back to packed counters: bit p of cell i goes to bit p of its
+                    // byte (CW = 1) or half word (CW = 2); a pass adds at most 247
+                    const uint32_t np = 32u - __clz(i2 - i1);
 #pragma unroll
-                for (int j = 0; j < kPer; ++j)
-                    if (w * kPer + j < nwords) s.cntw[w * kPer + j] += acc[j];
+                    for (int j = 0; j < kPer; ++j) {
+                        uint32_t acc = 0u;
+#pragma unroll
+                        for (int p = 0; p < 8; ++p) {
+                            if (uint32_t(p) >= np) break;
+                            const uint32_t bits = (pl[p] >> (kCells * j)) & ((1u << kCells) - 1u);
+                            if constexpr (CW == 1) acc += (bits * 0x00204081u & 0x01010101u) << p;
+                            else acc += (bits * 0x8001u & 0x10001u) << p;
+                        }
+                        if (w * kPer + j < nwords) s.cntw[w * kPer + j] += acc;
+                    }
+                }
             }
             __syncthreads();
         }
@@ -517,24 +551,33 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
             const uint32_t first = s.lvl_cur[t] - s.lvl_n[t];
             for (uint32_t c0 = 0; c0 < nc; c0 += NT) {
                 const uint32_t ci = c0 + tid;
-                uint32_t ms = 0, sz = 0, b = 0;
+                uint32_t ms = 0, sz = 0, b = 0, lev = 0;
                 if (ci < nc) {
                     b = lvl_cells[first + ci];
-                    ms = a.moff[b];
-                    sz = a.moff[b + 1] - ms;
+                    lev = cnt_at<CW>(s, b);
+                    // a member's score is at most its repetition-0 cell's level:
+                    // members of cells below the bound's score cannot enter
+                    if (lev >= bscore) {
+                        ms = a.moff[b];
+                        sz = a.moff[b + 1] - ms;
+                    }
                 }
                 uint32_t M;
                 const uint32_t pre = block_excl_scan<NT>(sz, s.wsum, &M);
-                s.c_start[tid] = ms;
+                s.c_start[tid] = ms - pre;        // record of member j of this cell: c_start + j
                 s.c_pre[tid] = pre;
-                s.c_cell[tid] = b | (cnt_at<CW>(s, b) << 16);   // cell and its count (its level)
+                s.c_cell[tid] = b | (lev << 16);  // cell and its count (its level)
                 const uint32_t ncc = min(uint32_t(NT), nc - c0);
                 __syncthreads();
-                // each (lane, u) walks member indices upwards: its cell index
-                // only moves forward, so the search starts from the last one
+                // Each warp walks its own contiguous slice of the member indices,
+                // 32 U at a time, so a lane's cell index moves forward by a cell or
+                // less per step (cells hold tens to hundreds of members).
+                const uint32_t per = ((M + NT / 32 - 1) / (NT / 32) + 31) & ~31u;
+                uint32_t jb = min(uint32_t(tid >> 5) * per, M);   // this warp's cursor (warp-uniform)
+                const uint32_t je = min(jb + per, M);
                 uint32_t hint[U];
 #pragma unroll
-                for (int u = 0; u < U; ++u) hint[u] = 0;
+                for (int u = 0; u < U; ++u) hint[u] = jb + uint32_t(u) * 32 + lane < je ? find_seg(s.c_pre, ncc, jb + uint32_t(u) * 32 + lane) : 0u;
                 // Members are decoded without per-round reservations: warps append
                 // freely while the buffer fill stays at or below hwm. A warp that
                 // sees it above hwm pauses; once every warp has paused or finished,
@@ -543,9 +586,8 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                 // (its iteration in flight, 32 U keys), so the buffer cannot
                 // overflow: hwm = cap - (NT + 32) U.
                 const uint32_t hwm = a.cap - uint32_t(NT + 32) * U;
-                uint32_t jb = tid & ~31u;         // this warp's cursor (warp-uniform)
                 for (;;) {
-                    while (jb < M) {
+                    while (jb < je) {
                         // the fill, read once per warp (lane 0) so the decision is warp-uniform
                         uint32_t fill = lane == 0 ? *reinterpret_cast<volatile uint32_t *>(&s.u[0]) : 0u;
                         fill = __shfl_sync(0xffffffffu, fill, 0);
@@ -555,8 +597,8 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                         bool in[U];
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
-                            const uint32_t j = jb + uint32_t(u) * NT + lane;
-                            in[u] = j < M;
+                            const uint32_t j = jb + uint32_t(u) * 32 + lane;
+                            in[u] = j < je;
                             cell[u] = 0;
                             if (in[u]) {
                                 uint32_t cs = hint[u];
@@ -564,7 +606,7 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                                 if (cs + 1 < ncc && s.c_pre[cs + 1] <= j) cs = find_seg(s.c_pre, ncc, j, cs);
                                 hint[u] = cs;
                                 cell[u] = s.c_cell[cs];
-                                load_record<RW>(a.mrec, s.c_start[cs] + (j - s.c_pre[cs]), w[u]);
+                                load_record<RW>(a.mrec, s.c_start[cs] + j, w[u]);
                             }
                         }
 #pragma unroll
@@ -604,7 +646,7 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                                 if (want) s.buf[base + __popc(wm & ((1u << lane) - 1u))] = key;
                             }
                         }
-                        jb += NT * U;
+                        jb += 32 * U;
                     }
                     __syncthreads();
                     const uint32_t nb0 = s.u[0];   // same value in every thread (read after the barrier)
