@@ -79,9 +79,9 @@ struct QSmem {
     uint32_t *lvl_n;     // nlev: repetition-0 cells per count
     uint32_t *lvl_cur;   // nlev
     uint32_t *rhist;     // 256: radix histogram
-    uint32_t *c_start;   // NT: member start of each cell of a chunk / list start
-    uint32_t *c_pre;     // NT + 1: exclusive prefix of member counts
-    uint32_t *c_cell;    // NT: repetition-0 group of each cell of a chunk
+    uint32_t *c_pre;     // NT + 4: exclusive prefix of member (list) lengths; c_pre[NT] = ~0
+    uint2 *c_rec;        // NT: per cell of a chunk {record base, cell | level << 16}
+    uint32_t *c_start;   // NT: per table of a chunk, list base (gather; shares c_rec's space)
     uint32_t *g_hl;      // NT: bitmap indices of the heavy tables of a chunk of tables
     uint32_t *wsum;      // NT / 32: block-scan scratch
     uint32_t *cntw;      // count words: 4 byte counts (CW = 1) or 2 16-bit counts (CW = 2) each
@@ -95,8 +95,8 @@ __host__ __device__ inline uint32_t q_count_words(uint32_t BR, int cw) { return 
 __host__ __device__ inline size_t qsmem_bytes(uint32_t cap, uint32_t kp, uint32_t BR, uint32_t B, int NT, uint32_t L,
                                               int cw)
 {
-    size_t b = size_t(cap) * 8 + size_t(kp) * 8 + 8 * 4 + 2 * size_t(q_nlev(L)) * 4 + 256 * 4 + NT * 4 +
-               (NT + 1) * 4 + NT * 4 + NT * 4 + (NT / 32) * 4;
+    size_t b = size_t(cap) * 8 + size_t(kp) * 8 + 8 * 4 + 2 * size_t(q_nlev(L)) * 4 + 256 * 4 +
+               (NT + 4) * 4 + 2 * NT * 4 + NT * 4 + (NT / 32) * 4;
     b = (b + 15) & ~size_t(15);
     b += size_t(q_count_words(BR, cw)) * 4;
     b += size_t(B) * 2;
@@ -114,10 +114,10 @@ __device__ inline QSmem carve_q(unsigned char *sm, uint32_t cap, uint32_t kp, ui
     s.lvl_n = s.u + 8;
     s.lvl_cur = s.lvl_n + nlev;
     s.rhist = s.lvl_cur + nlev;
-    s.c_start = s.rhist + 256;
-    s.c_pre = s.c_start + NT;
-    s.c_cell = s.c_pre + NT + 1;
-    s.g_hl = s.c_cell + NT;
+    s.c_pre = s.rhist + 256;
+    s.c_rec = reinterpret_cast<uint2 *>(s.c_pre + NT + 4);   // 8-byte aligned: offsets are even
+    s.c_start = reinterpret_cast<uint32_t *>(s.c_rec);
+    s.g_hl = reinterpret_cast<uint32_t *>(s.c_rec + NT);
     s.wsum = s.g_hl + NT;
     size_t o = (size_t)((unsigned char *)(s.wsum + NT / 32) - sm);
     o = (o + 15) & ~size_t(15);
@@ -369,9 +369,10 @@ __device__ void gather_counts(const QArgs &a, const QSmem &s, const uint32_t *qb
                 len = a.off[slot + 1] - beg;
             }
         }
+        if (tid == 0) s.c_pre[NT] = ~0u;   // ends every forward search of c_pre
         uint32_t total;
         const uint32_t pre = block_excl_scan<NT>(len, s.wsum, &total);
-        s.c_start[tid] = beg;
+        s.c_start[tid] = beg - pre;   // entry e of the flattened lists sits at c_start + e
         s.c_pre[tid] = pre;
         __syncthreads();
         const uint32_t nh = s.u[5];
@@ -429,15 +430,35 @@ __device__ void gather_counts(const QArgs &a, const QSmem &s, const uint32_t *qb
             __syncthreads();
         }
         const uint32_t nl = min(uint32_t(NT), a.L - l0);
-        for (uint32_t e0 = tid; e0 < total; e0 += NT * U) {
+        // each warp counts a contiguous slice of the flattened lists, so a lane's
+        // table index moves forward by at most a table per step (c_pre is total
+        // past the last table and ~0 at NT, which ends the search)
+        const uint32_t per = ((total + NT / 32 - 1) / (NT / 32) + 31) & ~31u;
+        const uint32_t eb0 = min(uint32_t(tid >> 5) * per, total);
+        const uint32_t ee = min(eb0 + per, total);
+        uint32_t hint[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t e = eb0 + uint32_t(u) * 32 + (tid & 31);
+            hint[u] = e < ee ? find_seg(s.c_pre, nl, e) : 0u;
+        }
+        for (uint32_t eb = eb0; eb < ee; eb += 32 * U) {
             uint32_t c[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const uint32_t e = e0 + uint32_t(u) * NT;
+                const uint32_t e = eb + uint32_t(u) * 32 + (tid & 31);
                 c[u] = kEmpty32;
-                if (e < total) {
-                    const uint32_t t = find_seg(s.c_pre, nl, e);
-                    c[u] = a.cells[s.c_start[t] + (e - s.c_pre[t])];
+                if (e < ee) {
+                    uint32_t t = hint[u];
+                    for (int step = 0; s.c_pre[t + 1] <= e; ++step) {
+                        if (step == 4) {
+                            t = find_seg(s.c_pre, nl, e, t + 1);
+                            break;
+                        }
+                        ++t;
+                    }
+                    hint[u] = t;
+                    c[u] = a.cells[s.c_start[t] + e];
                 }
             }
 #pragma unroll
@@ -562,11 +583,12 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                         sz = a.moff[b + 1] - ms;
                     }
                 }
+                if (tid == 0) s.c_pre[NT] = ~0u;   // ends every forward search of c_pre
                 uint32_t M;
                 const uint32_t pre = block_excl_scan<NT>(sz, s.wsum, &M);
-                s.c_start[tid] = ms - pre;        // record of member j of this cell: c_start + j
                 s.c_pre[tid] = pre;
-                s.c_cell[tid] = b | (lev << 16);  // cell and its count (its level)
+                // member j of this cell: record c_rec.x + j; the cell and its count (its level)
+                s.c_rec[tid] = make_uint2(ms - pre, b | (lev << 16));
                 const uint32_t ncc = min(uint32_t(NT), nc - c0);
                 __syncthreads();
                 // Each warp walks its own contiguous slice of the member indices,
@@ -578,20 +600,17 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                 uint32_t hint[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) hint[u] = jb + uint32_t(u) * 32 + lane < je ? find_seg(s.c_pre, ncc, jb + uint32_t(u) * 32 + lane) : 0u;
-                // Members are decoded without per-round reservations: warps append
-                // freely while the buffer fill stays at or below hwm. A warp that
-                // sees it above hwm pauses; once every warp has paused or finished,
-                // the block compacts and the warps resume from their own cursors.
-                // Once the fill passes hwm every warp appends at most once more
-                // (its iteration in flight, 32 U keys), so the buffer cannot
-                // overflow: hwm = cap - (NT + 32) U.
+                // Members are decoded without per-round reservations: a warp about
+                // to append reads the buffer fill first and appends only while it
+                // is at or below hwm. Above it the warp pauses; once every warp has
+                // paused or finished, the block compacts and the warps resume from
+                // their own cursors. Once the fill passes hwm every warp appends at
+                // most once more (the step it read the fill in, 32 U keys), so the
+                // buffer cannot overflow: hwm = cap - (NT + 32) U.
                 const uint32_t hwm = a.cap - uint32_t(NT + 32) * U;
                 for (;;) {
+                    const uint32_t smin = max(a.t_min, bscore);   // lower scores cannot enter
                     while (jb < je) {
-                        // the fill, read once per warp (lane 0) so the decision is warp-uniform
-                        uint32_t fill = lane == 0 ? *reinterpret_cast<volatile uint32_t *>(&s.u[0]) : 0u;
-                        fill = __shfl_sync(0xffffffffu, fill, 0);
-                        if (fill > hwm) break;
                         uint32_t w[U][RW];
                         uint32_t cell[U];
                         bool in[U];
@@ -601,23 +620,30 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                             in[u] = j < je;
                             cell[u] = 0;
                             if (in[u]) {
+                                // c_pre is M past the chunk's last cell and ~0 at NT
                                 uint32_t cs = hint[u];
-                                for (int step = 0; step < 4 && cs + 1 < ncc && s.c_pre[cs + 1] <= j; ++step) ++cs;
-                                if (cs + 1 < ncc && s.c_pre[cs + 1] <= j) cs = find_seg(s.c_pre, ncc, j, cs);
+                                for (int step = 0; s.c_pre[cs + 1] <= j; ++step) {
+                                    if (step == 4) {
+                                        cs = find_seg(s.c_pre, ncc, j, cs + 1);
+                                        break;
+                                    }
+                                    ++cs;
+                                }
                                 hint[u] = cs;
-                                cell[u] = s.c_cell[cs];
-                                load_record<RW>(a.mrec, s.c_start[cs] + j, w[u]);
+                                const uint2 cr = s.c_rec[cs];
+                                cell[u] = cr.y;
+                                load_record<RW>(a.mrec, cr.x + j, w[u]);
                             }
                         }
+                        uint64_t key[U];
+                        uint32_t wm[U], any = 0u;
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
-                            bool valid = false;
-                            uint32_t score = 0xFFFFu, last = 0, x = 0;
+                            bool want = false;
+                            key[u] = 0;
                             if (in[u]) {
-                                x = w[u][0];
                                 // repetition 0: the cell itself, at its level
-                                score = cell[u] >> 16;
-                                last = cell[u] & 0xFFFFu;
+                                uint32_t score = cell[u] >> 16, last = cell[u] & 0xFFFFu;
 #pragma unroll
                                 for (int r = 1; r < 2 * RW - 1; ++r) {
                                     if (r >= int(a.R)) break;
@@ -629,21 +655,28 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                                         score = v;
                                     }
                                 }
-                                // a score below the bound's cannot enter: skip the 64-bit key
-                                valid = score >= a.t_min && score >= bscore;
+                                if (score >= smin) {
+                                    key[u] = (uint64_t(kScoreMax - score) << 48) | (uint64_t(last) << 32) | w[u][0];
+                                    want = key[u] <= bound;
+                                }
                             }
-                            uint64_t key = 0;
-                            bool want = false;
-                            if (valid) {
-                                key = (uint64_t(kScoreMax - score) << 48) | (uint64_t(last) << 32) | x;
-                                want = key <= bound;
-                            }
-                            const uint32_t wm = __ballot_sync(0xffffffffu, want);
-                            if (wm) {
+                            wm[u] = __ballot_sync(0xffffffffu, want);
+                            any |= wm[u];
+                        }
+                        if (any) {
+                            // the fill, read once per warp (lane 0) so the decision is
+                            // warp-uniform; above hwm the warp pauses and redoes this
+                            // step after the compaction
+                            uint32_t fill = lane == 0 ? *reinterpret_cast<volatile uint32_t *>(&s.u[0]) : 0u;
+                            fill = __shfl_sync(0xffffffffu, fill, 0);
+                            if (fill > hwm) break;
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                if (!wm[u]) continue;
                                 uint32_t base = 0;
-                                if (lane == __ffs(wm) - 1) base = atomicAdd(&s.u[0], __popc(wm));
-                                base = __shfl_sync(0xffffffffu, base, __ffs(wm) - 1);
-                                if (want) s.buf[base + __popc(wm & ((1u << lane) - 1u))] = key;
+                                if (lane == __ffs(wm[u]) - 1) base = atomicAdd(&s.u[0], __popc(wm[u]));
+                                base = __shfl_sync(0xffffffffu, base, __ffs(wm[u]) - 1);
+                                if ((wm[u] >> lane) & 1u) s.buf[base + __popc(wm[u] & ((1u << lane) - 1u))] = key[u];
                             }
                         }
                         jb += 32 * U;
