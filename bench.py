@@ -499,6 +499,37 @@ def serving_runs(F, ix, c: dict, plain_qps: float, factors, check_sample: int = 
     return out
 
 
+# launch shapes of the fused form: CTA size x CTAs per SM (0: as many as fit)
+# x candidate-buffer entries (0: default), the set flinng_tune_query times
+TUNE_SHAPES = [(th, cp, cap) for th in (256, 128, 512) for cp in (0, 4, 2) for cap in (0, 4096, 1024)]
+
+
+def tune_cold(ix, nq: int, run, flush, stream, reps: int = 3) -> dict:
+    """The fused form's launch shape, chosen under the bench's own conditions:
+    L2 flushed before every timed launch, median of ``reps`` launches per shape
+    (flinng_tune_query times back-to-back launches on a warm L2, which can
+    favour another shape). Pins the winner with flinng_set_tuning."""
+    import torch
+    best = None
+    for th, cp, cap in TUNE_SHAPES:
+        ix.set_tuning(nq, th, cp, cap)
+        run()                                            # builds this shape's graph
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for r in range(reps):
+            flush.fill_(r + 11)
+            ev[r][0].record(stream)
+            run()
+            ev[r][1].record(stream)
+        torch.cuda.synchronize()
+        med = statistics.median(a.elapsed_time(b) for a, b in ev)
+        if best is None or med < best[0]:
+            best = (med, th, cp, cap)
+    ix.set_tuning(nq, *best[1:])
+    return {"threads": best[1], "ctas_per_sm": best[2], "cap": best[3],
+            "how": f"{len(TUNE_SHAPES)} shapes, median of {reps} launches each with L2 flushed before each"}
+
+
 def recall_target_point(F, c: dict, args, prec: int, dev, d_pts, d_q, tgt: dict, flush, ex_ids, ex_sims,
                         smp) -> dict:
     """The sweep's fastest point with recall@10 >= 0.9, measured like the main
@@ -522,6 +553,9 @@ def recall_target_point(F, c: dict, args, prec: int, dev, d_pts, d_q, tgt: dict,
 
     def fused():
         F._check(ix.lib.flinng_query(ix.h, C.byref(fp), nq, None, k, ids.data_ptr(), sc.data_ptr(), 1))
+
+    if tuning["threads"]:
+        tuning = tune_cold(ix, nq, fused, flush, stream)
 
     def plain():
         F._check(ix.lib.flinng_hash(ix.h, C.byref(fp), nq, qb.data_ptr(), None, None, 1))
@@ -808,6 +842,8 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     # the fused form: autotuned launch shape, CUDA graph per batch-size class
     tuning = ix.tune(d_q, k)
     ix.set_query_mode(F.QUERY_GRAPH)
+    if tuning["threads"]:
+        tuning = tune_cold(ix, nq, step_fused, flush, stream)
     # the two forms return the same results
     step_fused()
     step_plain(torch.cuda.Event(enable_timing=True))

@@ -222,6 +222,16 @@ int flinng_set_query_mode(flinng_index *idx, uint32_t mode);
 int flinng_tune_query(flinng_index *idx, const flinng_points *q, uint32_t nq,
                       uint32_t k_max, int on_device, uint32_t *chosen);
 
+/* Set the fused query's launch shape for batches of nq's size class (the
+ * power of two at or above nq) instead of tuning it, e.g. to a shape tuned
+ * offline or under other cache conditions. threads: 128, 256 or 512;
+ * ctas_per_sm: 0 (as many as fit) to 16; cap: candidate buffer entries, 0
+ * (default) or a power of two in [64, 8192] (raised to the decode's minimum
+ * when smaller). Results never depend on the shape. FLINNG_ERR_INVALID_ARG on
+ * any other value. */
+int flinng_set_tuning(flinng_index *idx, uint32_t nq, uint32_t threads, uint32_t ctas_per_sm,
+                      uint32_t cap);
+
 /* ---------------------------------------------------------------------- */
 /* Stage entry points, for parity checks of each step against a reference */
 /* ---------------------------------------------------------------------- */

@@ -451,6 +451,21 @@ int flinng_tune_query(flinng_index *idx, const flinng_points *q, uint32_t nq, ui
     return FLINNG_OK;
 }
 
+int flinng_set_tuning(flinng_index *idx, uint32_t nq, uint32_t threads, uint32_t ctas_per_sm, uint32_t cap)
+{
+    if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
+    if (nq == 0) return set_error(FLINNG_ERR_INVALID_ARG, "set_tuning: nq is 0");
+    if (threads != 128 && threads != 256 && threads != 512)
+        return set_error(FLINNG_ERR_INVALID_ARG, "set_tuning: threads must be 128, 256 or 512");
+    if (ctas_per_sm > 16) return set_error(FLINNG_ERR_INVALID_ARG, "set_tuning: ctas_per_sm > 16");
+    if (cap != 0 && (cap < 64 || cap > 8192 || (cap & (cap - 1)) != 0))
+        return set_error(FLINNG_ERR_INVALID_ARG, "set_tuning: cap must be 0 or a power of two in [64, 8192]");
+    uint32_t bucket = 0;
+    while ((1u << bucket) < nq) ++bucket;
+    idx->tuning[bucket] = QueryTuning{threads, ctas_per_sm, cap, 1};
+    return FLINNG_OK;
+}
+
 int flinng_build(flinng_index *idx, const flinng_points *pts, uint64_t n, const uint32_t *perm,
                  int on_device)
 {

@@ -102,6 +102,7 @@ _SIGS = {
                                       C.c_void_p, C.c_void_p, C.c_int]),
     "flinng_kernel_launches": (C.c_uint64, []),
     "flinng_set_query_mode": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "flinng_set_tuning": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]),
     "flinng_tune_query": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint32, C.c_uint32,
                                     C.c_int, C.c_void_p]),
     "flinng_server_create": (C.c_int, [C.POINTER(flinng_server_config), C.POINTER(C.c_void_p)]),
@@ -379,6 +380,10 @@ class Index:
         ch = np.zeros(3, np.uint32)
         _check(self.lib.flinng_tune_query(self.h, C.byref(fp), nq, k_max, dev, ch.ctypes.data))
         return {"threads": int(ch[0]), "ctas_per_sm": int(ch[1]), "cap": int(ch[2])}
+
+    def set_tuning(self, nq: int, threads: int, ctas_per_sm: int = 0, cap: int = 0):
+        """Pin the fused query's launch shape for batches of nq's size class."""
+        _check(self.lib.flinng_set_tuning(self.h, nq, threads, ctas_per_sm, cap))
 
     def hash_stats(self):
         a, b = C.c_uint64(), C.c_uint64()

@@ -337,6 +337,30 @@ def test_graph_replay_and_tuning_keep_results(F):
     assert np.array_equal(ids, ref[(0, 300)][0])
 
 
+def test_pinned_shapes_keep_results(F):
+    # every launch shape flinng_set_tuning accepts gives the plain form's
+    # results, in graph and fused modes; other values are refused
+    N, nq, R, B, L, K, W = 3000, 300, 2, 300, 32, 2, 15
+    pts, q, dp, perm = sets_case(42, N, nq, R, L, K)
+    ix = F.Index("jaccard", R, B, L, K, capacity=N, params=dp, W=W)
+    ix.build(pts, perm)
+    ix.set_query_mode(0)
+    rid, rsc = ix.query(q, 30)
+    for th in (128, 256, 512):
+        for cp in (0, 1, 4):
+            for cap in (0, 64, 1024, 8192):
+                ix.set_tuning(nq, th, cp, cap)
+                for mode in (1, 2):
+                    ix.set_query_mode(mode)
+                    ids, sc = ix.query(q, 30)
+                    assert np.array_equal(ids, rid) and np.array_equal(sc, rsc), (th, cp, cap, mode)
+    for bad in [(nq, 64, 0, 0), (nq, 1024, 0, 0), (nq, 256, 17, 0), (nq, 256, 0, 100), (nq, 256, 0, 16384),
+                (0, 256, 0, 0)]:
+        with pytest.raises(F.FlinngError) as e:
+            ix.set_tuning(*bad)
+        assert e.value.code == F.ERR_INVALID_ARG
+
+
 def test_graph_mode_cosine_stats_reset(F):
     pts, q, w, perm = dense_case(41, 800, 40, 50, 2, 20, 6, 7)
     q[0] = 0.0
