@@ -23,7 +23,12 @@
  *    of the current device; the call is then asynchronous on the index's
  *    stream (synchronise that stream before reading outputs or freeing
  *    inputs). 0 means every caller buffer is host memory; the call copies
- *    in, computes, copies out and returns after the stream is idle.
+ *    in, computes, copies out and returns after the stream is idle. In
+ *    flinng_query, host buffers that are page-locked (cudaHostAlloc,
+ *    cudaHostRegister) skip the copies: the query kernel writes the outputs
+ *    in place, and reads the queries in place where it loads each element
+ *    once (Jaccard queries; cosine queries hashed per CTA, see
+ *    flinng_set_query_mode).
  *  - Point ids are insertion order: the first build gives ids 0..n-1, each
  *    insert continues the numbering.
  *  - Cell ids are r * B + b for repetition r and group b; they are 16-bit

@@ -176,6 +176,50 @@ int stage_points(flinng_index *ix, const flinng_points *pts, uint64_t n, int on_
     return FLINNG_OK;
 }
 
+// Device address of a host buffer of the given size when all of it is
+// page-locked memory known to CUDA (cudaHostAlloc, cudaHostRegister): kernels
+// can then read or write it in place over the host link. nullptr otherwise
+// (pageable memory, or a range that leaves the allocation).
+template <class T>
+T *pinned_view(T *p, size_t bytes)
+{
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes a0{}, a1{};
+    const char *first = reinterpret_cast<const char *>(p);
+    if (cudaPointerGetAttributes(&a0, first) != cudaSuccess ||
+        cudaPointerGetAttributes(&a1, first + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+        return nullptr;
+    const char *d0 = static_cast<const char *>(a0.devicePointer), *d1 = static_cast<const char *>(a1.devicePointer);
+    if (d1 - d0 != ptrdiff_t(bytes - 1)) return nullptr;
+    return reinterpret_cast<T *>(const_cast<char *>(d0));
+}
+
+// A host batch read in place by kernels that load each element once (the
+// fused query's per-CTA hashing, DOPH hashing): true when its buffers are
+// page-locked, with s set to their device addresses; no staging copy.
+bool pinned_points(const flinng_index *ix, const flinng_points *pts, uint64_t n, Staged &s)
+{
+    if (n == 0) return false;
+    if (ix->cfg.metric == FLINNG_COSINE_SRP) {
+        const float *x = pinned_view(pts->x, ((n - 1) * pts->ld + ix->cfg.dim) * sizeof(float));
+        if (!x) return false;
+        s.x = x;
+        s.ld = pts->ld;
+        return true;
+    }
+    const uint64_t ne = pts->off[n];
+    const uint64_t *off = pinned_view(pts->off, (n + 1) * sizeof(uint64_t));
+    const uint32_t *el = ne ? pinned_view(pts->elems, ne * sizeof(uint32_t)) : nullptr;
+    if (!off || (ne && !el)) return false;
+    s.off = off;
+    s.elems = el;
+    return true;
+}
+
 int hash_staged(flinng_index *ix, const Staged &s, uint64_t n, uint32_t *buckets, uint32_t *values,
                 float *proj, void *hws, size_t hws_bytes)
 {
@@ -553,10 +597,11 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
                        (idx->query_mode == FLINNG_QUERY_FUSED || idx->query_mode == FLINNG_QUERY_GRAPH);
     Staged fs;
     if (fused) {
-        FL_TRY(stage_points(idx, q, nq, on_device, c, fs));
+        if (on_device || !pinned_points(idx, q, nq, fs)) FL_TRY(stage_points(idx, q, nq, on_device, c, fs));
     } else if (q) {
         Staged s;
-        FL_TRY(stage_points(idx, q, nq, on_device, c, s));
+        const bool in_place = !on_device && idx->cfg.metric == FLINNG_JACCARD_DOPH && pinned_points(idx, q, nq, s);
+        if (!in_place) FL_TRY(stage_points(idx, q, nq, on_device, c, s));
         qb = c.take<uint32_t>(uint64_t(nq) * L);
         const size_t hb = hash_ws_bytes(idx, nq);
         void *hws = c.take<char>(hb);
@@ -570,14 +615,24 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
     const uint32_t *dk = k;
     uint32_t *dids = out_ids;
     uint16_t *dsc = out_scores;
+    bool out_in_place = false;
     if (!on_device) {
         if (k) {
             uint32_t *t = c.take<uint32_t>(nq);
             FL_CUDA(cudaMemcpyAsync(t, k, nq * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
             dk = t;
         }
-        dids = c.take<uint32_t>(uint64_t(nq) * k_max);
-        dsc = out_scores ? c.take<uint16_t>(uint64_t(nq) * k_max) : nullptr;
+        // page-locked outputs are written in place by the query kernel
+        uint32_t *pid = pinned_view(out_ids, size_t(nq) * k_max * sizeof(uint32_t));
+        uint16_t *psc = out_scores ? pinned_view(out_scores, size_t(nq) * k_max * sizeof(uint16_t)) : nullptr;
+        out_in_place = pid && (!out_scores || psc);
+        if (out_in_place) {
+            dids = pid;
+            dsc = psc;
+        } else {
+            dids = c.take<uint32_t>(uint64_t(nq) * k_max);
+            dsc = out_scores ? c.take<uint16_t>(uint64_t(nq) * k_max) : nullptr;
+        }
     }
     if (fused) {
         FusedQuery fq{nq, fs.x, fs.ld, fs.off, fs.elems};
@@ -593,7 +648,7 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
         FL_TRY(query_launch(idx, qb, nq, dk, k_max, dids, dsc));
     }
     if (!on_device) {
-        if (k_max) {
+        if (k_max && !out_in_place) {
             FL_CUDA(cudaMemcpyAsync(out_ids, dids, uint64_t(nq) * k_max * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
             if (out_scores)
                 FL_CUDA(cudaMemcpyAsync(out_scores, dsc, uint64_t(nq) * k_max * sizeof(uint16_t),

@@ -322,10 +322,24 @@ class Index:
         _check(self.lib.flinng_hash(self.h, C.byref(fp), n, _ptr(b), _ptr(v), _ptr(pr), dev))
         return b, v, pr
 
-    def query(self, q, k_max: int, k=None):
+    def query(self, q, k_max: int, k=None, out=None):
+        """Top-k_max of each query. out: optional (ids, scores) buffers of the
+        queries' kind (nq x k_max uint32 and uint16 arrays for host queries,
+        int32 and int16 CUDA tensors for device queries), filled and returned;
+        page-locked host buffers are written in place by the kernel."""
         fp, nq, dev, keep = self._points(q)
-        ids = self._out(dev, (nq, k_max), np.uint32)
-        sc = self._out(dev, (nq, k_max), np.uint16)
+        if out is None:
+            ids = self._out(dev, (nq, k_max), np.uint32)
+            sc = self._out(dev, (nq, k_max), np.uint16)
+        else:
+            ids, sc = out
+            if tuple(ids.shape) != (nq, k_max) or tuple(sc.shape) != (nq, k_max):
+                raise ValueError("out buffers must be nq x k_max")
+            if bool(_is_cuda(ids)) != bool(dev) or bool(_is_cuda(sc)) != bool(dev):
+                raise ValueError("out buffers must live where the queries do")
+            if not dev and (ids.dtype != np.uint32 or sc.dtype != np.uint16 or not ids.flags.c_contiguous
+                            or not sc.flags.c_contiguous):
+                raise ValueError("host out buffers must be C-contiguous uint32 and uint16 arrays")
         kk = None if k is None else (k if _is_cuda(k) else _np(k, np.uint32))
         _check(self.lib.flinng_query(self.h, C.byref(fp), nq, _ptr(kk), k_max, _ptr(ids), _ptr(sc), dev))
         return ids, sc

@@ -361,6 +361,54 @@ def test_pinned_shapes_keep_results(F):
         assert e.value.code == F.ERR_INVALID_ARG
 
 
+def _pinned(a):
+    import torch
+    a = np.ascontiguousarray(a)
+    t = torch.from_numpy(a.view({1: np.int8, 2: np.int16, 4: np.int32, 8: np.int64}[a.itemsize]))
+    return t.pin_memory().numpy().view(a.dtype)
+
+
+def test_pinned_host_buffers_in_place(F):
+    # page-locked queries and results are read and written in place by the
+    # kernels; every mix of pinned and pageable buffers gives the staged results
+    N, nq, R, B, L, K, W = 3000, 300, 2, 300, 32, 2, 15
+    pts, q, dp, perm = sets_case(43, N, nq, R, L, K)
+    ix = F.Index("jaccard", R, B, L, K, capacity=N, params=dp, W=W)
+    ix.build(pts, perm)
+    ix.set_query_mode(0)
+    rid, rsc = ix.query(q, 30)                      # pageable: staged by copies
+    pq = (_pinned(q[0]), _pinned(q[1]))
+    oi, osc = _pinned(np.zeros((nq, 30), np.uint32)), _pinned(np.zeros((nq, 30), np.uint16))
+    for mode in (0, 1, 2):
+        ix.set_query_mode(mode)
+        for qq, out in ((pq, (oi, osc)), (pq, None), (q, (oi, osc))):
+            if out is not None:
+                oi.fill(7)
+                osc.fill(7)
+            ids, sc = ix.query(qq, 30, out=out)
+            if out is not None:
+                assert ids is oi and sc is osc
+            assert np.array_equal(ids, rid) and np.array_equal(sc, rsc), mode
+    # a pinned sub-range (interior pointers) of a larger batch
+    big = _pinned(np.zeros((nq + 5, 30), np.uint32))
+    ids, _ = ix.query(pq, 30, out=(big[5:], _pinned(np.zeros((nq, 30), np.uint16))))
+    assert np.array_equal(big[5:], rid)
+    # cosine: the fused form reads pinned queries in place, the plain form stages them
+    pts, qd, w, perm = dense_case(44, 2000, 64, 150, 2, 40, 8, 10)
+    jx = F.Index("cosine", 2, 40, 8, 10, capacity=2000, params=w, dim=64)
+    jx.build(pts, perm)
+    jx.set_query_mode(0)
+    cid, csc = jx.query(qd, 12)
+    pqd = _pinned(qd)
+    ci, cs = _pinned(np.zeros((150, 12), np.uint32)), _pinned(np.zeros((150, 12), np.uint16))
+    for mode in (0, 1, 2):
+        jx.set_query_mode(mode)
+        ids, sc = jx.query(pqd, 12, out=(ci, cs))
+        assert np.array_equal(ids, cid) and np.array_equal(sc, csc), mode
+    with pytest.raises(ValueError):
+        jx.query(pqd, 12, out=(ci[:, :5], cs))
+
+
 def test_graph_mode_cosine_stats_reset(F):
     pts, q, w, perm = dense_case(41, 800, 40, 50, 2, 20, 6, 7)
     q[0] = 0.0
