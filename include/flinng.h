@@ -152,6 +152,23 @@ int flinng_insert(flinng_index *idx, const flinng_points *pts, uint64_t n,
                   const uint32_t *perm, int on_device);
 
 /*
+ * Build (replacing the index) or insert with the group design given
+ * outright instead of Alg. 1's permutations. The framework takes any
+ * non-adaptive design (Sec. 3.1); with one test per point and repetition,
+ * Alg. 2's AND over the R tests and Alg. 3's relaxed decode apply unchanged.
+ * Groups may be of any size, some empty, e.g. each point's group drawn
+ * independently per repetition.
+ * groups: R x n uint16, row-major: groups[r * n + i] is the group (< B) of
+ * point i of this batch in repetition r (its cell is r * B + group).
+ * Errors: as flinng_build / flinng_insert; INVALID_ARG (index unchanged) if
+ * a group id is >= B or groups is null with n > 0.
+ */
+int flinng_build_groups(flinng_index *idx, const flinng_points *pts, uint64_t n,
+                        const uint16_t *groups, int on_device);
+int flinng_insert_groups(flinng_index *idx, const flinng_points *pts, uint64_t n,
+                         const uint16_t *groups, int on_device);
+
+/*
  * Batched query (Sec. 5 with Alg. 3): hash each query once, count per cell
  * the tables whose bucket list holds the cell, and return the points in
  * Alg. 3's order - cells by count descending (ties: cell id ascending),

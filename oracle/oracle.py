@@ -144,6 +144,20 @@ def groups(perm, B: int, n_old: int = 0, gid=None):
     return gid
 
 
+def design_groups(groups, B: int):
+    """Cells of a non-adaptive design given outright, one test per point and
+    repetition (Sec. 3.1: the framework takes any non-adaptive design, the
+    doubly regular one of Alg. 1 being one case). Row r of ``groups`` (R, n)
+    holds each point's group in repetition r; returned point-major (n, R)
+    uint16 like groups()."""
+    g = np.asarray(groups)
+    if g.ndim != 2:
+        raise ValueError("groups must be R x n")
+    if g.size and (int(g.min()) < 0 or int(g.max()) >= B):
+        raise ValueError("a group id is outside [0, B)")
+    return np.ascontiguousarray(g.T.astype(np.uint16))
+
+
 def members(gid, B: int):
     gid = _c(gid, np.uint16)
     N, R = gid.shape
@@ -228,6 +242,28 @@ class OracleIndex:
         self.moff, self.mem = members(self.gid, self.B)
 
     build = insert
+
+    def insert_groups(self, pts, groups):
+        """Insert with the points' groups given (an arbitrary non-adaptive
+        design, one test per repetition) instead of Alg. 1's permutations."""
+        g = design_groups(groups, self.B)
+        if g.shape[1] != self.R:
+            raise ValueError("groups must have R rows")
+        bk = self.hash(pts)
+        if bk.shape[0] != g.shape[0]:
+            raise ValueError("groups must have one column per point")
+        self.gid = np.concatenate([self.gid, g]) if self.N else g
+        self.buckets = np.concatenate([self.buckets, bk])
+        self.N += bk.shape[0]
+        self.off, self.cells = build_csr(self.buckets, self.gid, self.B, self.W)
+        self.moff, self.mem = members(self.gid, self.B)
+
+    def build_groups(self, pts, groups):
+        """A fresh index over pts with the given design."""
+        self.N = 0
+        self.buckets = np.zeros((0, self.L), np.uint32)
+        self.gid = np.zeros((0, self.R), np.uint16)
+        self.insert_groups(pts, groups)
 
     def query_buckets(self, qb, k_max: int, k=None):
         qb = _c(qb, np.uint32)

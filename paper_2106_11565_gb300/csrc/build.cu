@@ -66,6 +66,29 @@ __global__ void k_groups(const uint32_t *__restrict__ perm, uint32_t R, uint64_t
     }
 }
 
+// Groups given outright (any non-adaptive design with one test per point and
+// repetition, Sec. 3.1): row r of groups (R x n) holds the new points' groups
+// in repetition r. Flag bit 8: a group id >= B (nothing is written then by
+// the caller, which checks first).
+__global__ void k_check_groups(const uint16_t *__restrict__ groups, uint64_t total, uint32_t B,
+                               uint32_t *__restrict__ flag)
+{
+    for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+         t += uint64_t(gridDim.x) * blockDim.x)
+        if (groups[t] >= B) atomicOr(flag, 8u);
+}
+
+__global__ void k_groups_given(const uint16_t *__restrict__ groups, uint32_t R, uint64_t n,
+                               uint64_t n_old, uint32_t rp, uint16_t *__restrict__ gid)
+{
+    const uint64_t total = uint64_t(R) * n;
+    for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+         t += uint64_t(gridDim.x) * blockDim.x) {
+        const uint64_t r = t / n, i = t % n;
+        gid[(n_old + i) * rp + r] = groups[t];
+    }
+}
+
 __global__ void k_member_hist(const uint16_t *__restrict__ gid, uint64_t N, uint32_t R,
                               uint32_t B, uint32_t rp, uint32_t *__restrict__ cnt)
 {
@@ -356,7 +379,22 @@ size_t insert_workspace_bytes(const flinng_index *ix)
     return carve_bytes<uint32_t>(ns) + carve_bytes<uint32_t>(ix->BR + 1) + scan_workspace_bytes(big);
 }
 
-int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *perm,
+int check_groups(flinng_index *ix, const uint16_t *groups, uint64_t n)
+{
+    const cudaStream_t st = ix->stream;
+    if (n == 0) return FLINNG_OK;
+    FL_CUDA(cudaMemsetAsync(ix->flag, 0, 4, st));
+    k_check_groups<<<thread_blocks(uint64_t(ix->cfg.R) * n), 256, 0, st>>>(groups, uint64_t(ix->cfg.R) * n,
+                                                                         ix->cfg.B, ix->flag);
+    count_launch();
+    FL_CUDA(cudaGetLastError());
+    FL_CUDA(cudaMemcpyAsync(ix->h_flag, ix->flag, 4, cudaMemcpyDeviceToHost, st));
+    FL_CUDA(cudaStreamSynchronize(st));
+    if (*ix->h_flag & 8u) return set_error(FLINNG_ERR_INVALID_ARG, "groups: a group id is >= B");
+    return FLINNG_OK;
+}
+
+int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *perm, const uint16_t *groups,
                   uint64_t n, void *ws)
 {
     const cudaStream_t st = ix->stream;
@@ -368,9 +406,12 @@ int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *per
     uint32_t *mcur = c.take<uint32_t>(BR + 1);
     void *scan_ws = c.base + ((c.used + 255) & ~size_t(255));
 
-    // Alg. 1: groups of the new points
+    // groups of the new points: Alg. 1 from the permutations, or given outright
     if (n > 0) {
-        k_groups<<<thread_blocks(uint64_t(R) * n), 256, 0, st>>>(perm, R, n, n_old, B, rp, ix->gid);
+        if (groups)
+            k_groups_given<<<thread_blocks(uint64_t(R) * n), 256, 0, st>>>(groups, R, n, n_old, rp, ix->gid);
+        else
+            k_groups<<<thread_blocks(uint64_t(R) * n), 256, 0, st>>>(perm, R, n, n_old, B, rp, ix->gid);
         count_launch();
         FL_CUDA(cudaGetLastError());
     }

@@ -242,7 +242,8 @@ __global__ void k_check_buckets(const uint32_t *__restrict__ b, uint64_t n, uint
 }
 
 int insert_common(flinng_index *ix, const flinng_points *pts, uint64_t n, const uint32_t *perm,
-                  int on_device, bool reset, const uint32_t *given_buckets = nullptr)
+                  int on_device, bool reset, const uint32_t *given_buckets = nullptr,
+                  const uint16_t *groups = nullptr)
 {
     if (!ix) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
     const uint64_t base = reset ? 0 : ix->n_points;
@@ -251,25 +252,34 @@ int insert_common(flinng_index *ix, const flinng_points *pts, uint64_t n, const 
                          (unsigned long long)base, (unsigned long long)n,
                          (unsigned long long)ix->cfg.capacity);
     if (!given_buckets) FL_TRY(check_points(ix, pts, n, on_device));
-    if (n > 0 && !perm) return set_error(FLINNG_ERR_INVALID_ARG, "insert: perm is null");
+    if (n > 0 && !perm && !groups) return set_error(FLINNG_ERR_INVALID_ARG, "insert: perm is null");
     const cudaStream_t st = ix->stream;
     const uint32_t R = ix->cfg.R, L = ix->cfg.L;
     const size_t need = (given_buckets ? 0 : stage_bytes(ix, pts, n, on_device)) + carve_bytes<uint32_t>(uint64_t(R) * n) +
+                        carve_bytes<uint16_t>(uint64_t(R) * n) +
                         carve_bytes<uint32_t>(n * L) + perm_check_workspace_bytes(R, n) +
                         hash_ws_bytes(ix, n) + insert_workspace_bytes(ix) + 4096;
     FL_TRY(ws_reserve(ix, need));
     Carver c(ix->ws.ptr, ix->ws.bytes);
     Staged s;
     if (!given_buckets) FL_TRY(stage_points(ix, pts, n, on_device, c, s));
-    const uint32_t *dperm = perm;
+    const uint32_t *dperm = groups ? nullptr : perm;
+    const uint16_t *dgroups = groups;
     if (!on_device && n > 0) {
-        uint32_t *p = c.take<uint32_t>(uint64_t(R) * n);
-        FL_CUDA(cudaMemcpyAsync(p, perm, uint64_t(R) * n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-        dperm = p;
+        if (groups) {
+            uint16_t *g = c.take<uint16_t>(uint64_t(R) * n);
+            FL_CUDA(cudaMemcpyAsync(g, groups, uint64_t(R) * n * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
+            dgroups = g;
+        } else {
+            uint32_t *p = c.take<uint32_t>(uint64_t(R) * n);
+            FL_CUDA(cudaMemcpyAsync(p, perm, uint64_t(R) * n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+            dperm = p;
+        }
     }
     uint32_t *buckets = c.take<uint32_t>(n * L);
     void *pws = c.take<char>(perm_check_workspace_bytes(R, n));
-    FL_TRY(check_perm(ix, dperm, n, pws));
+    if (groups) FL_TRY(check_groups(ix, dgroups, n));
+    else FL_TRY(check_perm(ix, dperm, n, pws));
     const size_t hb = hash_ws_bytes(ix, n);
     void *hws = c.take<char>(hb);
     void *iws = c.take<char>(insert_workspace_bytes(ix));
@@ -294,7 +304,7 @@ int insert_common(flinng_index *ix, const flinng_points *pts, uint64_t n, const 
         ix->n_cells = 0;
     }
     if (!given_buckets) FL_TRY(hash_staged(ix, s, n, buckets, nullptr, nullptr, hws, hb));
-    FL_TRY(insert_hashed(ix, buckets, dperm, n, iws));
+    FL_TRY(insert_hashed(ix, buckets, dperm, dgroups, n, iws));
     return FLINNG_OK;
 }
 
@@ -527,6 +537,20 @@ int flinng_insert(flinng_index *idx, const flinng_points *pts, uint64_t n, const
                   int on_device)
 {
     return insert_common(idx, pts, n, perm, on_device, false);
+}
+
+int flinng_build_groups(flinng_index *idx, const flinng_points *pts, uint64_t n, const uint16_t *groups,
+                        int on_device)
+{
+    if (n > 0 && !groups) return set_error(FLINNG_ERR_INVALID_ARG, "build_groups: groups is null");
+    return insert_common(idx, pts, n, nullptr, on_device, true, nullptr, groups);
+}
+
+int flinng_insert_groups(flinng_index *idx, const flinng_points *pts, uint64_t n, const uint16_t *groups,
+                         int on_device)
+{
+    if (n > 0 && !groups) return set_error(FLINNG_ERR_INVALID_ARG, "insert_groups: groups is null");
+    return insert_common(idx, pts, n, nullptr, on_device, false, nullptr, groups);
 }
 
 int flinng_hash(flinng_index *idx, const flinng_points *pts, uint64_t n, uint32_t *out_buckets,

@@ -102,6 +102,8 @@ _SIGS = {
                                       C.c_void_p, C.c_void_p, C.c_int]),
     "flinng_kernel_launches": (C.c_uint64, []),
     "flinng_set_query_mode": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "flinng_build_groups": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint64, C.c_void_p, C.c_int]),
+    "flinng_insert_groups": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint64, C.c_void_p, C.c_int]),
     "flinng_set_tuning": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]),
     "flinng_tune_query": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint32, C.c_uint32,
                                     C.c_int, C.c_void_p]),
@@ -304,6 +306,19 @@ class Index:
         fp, n, dev, keep = self._points(pts)
         perm = perm if _is_cuda(perm) else _np(perm, np.uint32)
         _check(self.lib.flinng_insert(self.h, C.byref(fp), n, _ptr(perm), dev))
+
+    def build_groups(self, pts, groups):
+        """Build with the design given outright: groups (R x n uint16), row r
+        holding each point's group in repetition r."""
+        fp, n, dev, keep = self._points(pts)
+        g = groups if _is_cuda(groups) else _np(groups, np.uint16)
+        _check(self.lib.flinng_build_groups(self.h, C.byref(fp), n, _ptr(g), dev))
+
+    def insert_groups(self, pts, groups):
+        """Insert with the new points' groups given (R x n uint16)."""
+        fp, n, dev, keep = self._points(pts)
+        g = groups if _is_cuda(groups) else _np(groups, np.uint16)
+        _check(self.lib.flinng_insert_groups(self.h, C.byref(fp), n, _ptr(g), dev))
 
     def _out(self, dev, shape, dt):
         if dev:

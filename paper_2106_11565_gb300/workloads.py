@@ -73,6 +73,15 @@ def group_permutations(seed: int, R: int, n: int, batch: int = 0) -> np.ndarray:
     return out
 
 
+def random_design(seed: int, R: int, n: int, B: int, batch: int = 0) -> np.ndarray:
+    """A non-adaptive design other than Alg. 1's doubly regular one: each
+    point joins one group per repetition, drawn uniformly and independently
+    (groups of Binomial(n, 1/B) size, some possibly empty). Shape (R, n)
+    uint16: row r holds the points' groups in repetition r."""
+    rng = np.random.default_rng([seed, 5, batch])
+    return rng.integers(0, B, size=(R, n)).astype(np.uint16)
+
+
 # --------------------------------------------------------------------------
 # dense vectors
 # --------------------------------------------------------------------------

@@ -160,6 +160,64 @@ def test_insert_equals_oracle_insert(F):
     assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc)
 
 
+def test_given_design_bit_exact(F):
+    """Sec. 3.1: a design given outright (each point's group drawn uniformly
+    and independently per repetition: unequal and empty groups), by build,
+    by build then insert, and with every point in one group; the index and
+    every query mode equal the oracle's. A group id >= B is refused and the
+    index is left as it was."""
+    import torch
+    N, nq, R, B, L, K, W = 3000, 200, 3, 400, 32, 2, 15
+    pts, q, dp, perm = sets_case(45, N, nq, R, L, K)
+    g = WL.random_design(45, R, N, B)
+    assert np.bincount(g[0], minlength=B).min() == 0 or np.bincount(g[0], minlength=B).max() > N // B + 1
+
+    def sets(lo, hi):
+        off, el = pts
+        return (off[lo:hi + 1] - off[lo]).astype(np.uint64), np.ascontiguousarray(el[off[lo]:off[hi]])
+
+    def check(ix, o):
+        ex = ix.export()
+        assert np.array_equal(ex["gid"], o.gid)
+        assert np.array_equal(ex["off"], o.off) and np.array_equal(ex["cells"], o.cells)
+        oids, osc = o.query(q, 30)
+        for mode in (0, 1, 2):
+            ix.set_query_mode(mode)
+            ids, sc = ix.query(q, 30)
+            assert np.array_equal(u32(ids), oids) and np.array_equal(sc, osc), mode
+
+    o = O.OracleIndex("jaccard", R, B, L, K, W, doph=dp)
+    o.build_groups(pts, g)
+    ix = F.Index("jaccard", R, B, L, K, capacity=N, params=dp, W=W)
+    ix.build_groups(pts, g)
+    check(ix, o)
+    # build then insert, groups in device memory
+    jx = F.Index("jaccard", R, B, L, K, capacity=N + 100, params=dp, W=W)
+    d_off = lambda a: torch.from_numpy(a.view(np.int64)).cuda()
+    d_el = lambda a: torch.from_numpy(a.view(np.int32)).cuda()
+    d_g = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int16)).cuda()
+    a_off, a_el = sets(0, 1800)
+    b_off, b_el = sets(1800, N)
+    jx.build_groups((d_off(a_off), d_el(a_el)), d_g(g[:, :1800]))
+    jx.insert_groups((d_off(b_off), d_el(b_el)), d_g(g[:, 1800:]))
+    torch.cuda.synchronize()
+    check(jx, o)
+    # a refused group id leaves the index as it was
+    bad = g[:, :10].copy()
+    bad[1, 3] = B
+    with pytest.raises(F.FlinngError) as e:
+        jx.insert_groups(sets(0, 10), bad)
+    assert e.value.code == F.ERR_INVALID_ARG
+    check(jx, o)
+    # every point in group 0: one cell of N members per repetition
+    z = np.zeros((R, N), np.uint16)
+    o2 = O.OracleIndex("jaccard", R, B, L, K, W, doph=dp)
+    o2.build_groups(pts, z)
+    kx = F.Index("jaccard", R, B, L, K, capacity=N, params=dp, W=W)
+    kx.build_groups(pts, z)
+    check(kx, o2)
+
+
 # ------------------------------------------------------------------ query
 
 def test_counts_bit_exact(F):

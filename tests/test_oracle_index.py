@@ -286,3 +286,85 @@ def test_counts_wide_equal_direct_definition():
         c2 = O.counts_direct(buckets, gid, B, qb)
         assert np.array_equal(c1, c2)
         assert c1.max() == L and c1.dtype == np.uint16
+
+
+# ------------------------------------------------------------ other designs
+#
+# Sec. 3.1: the framework takes any non-adaptive design. With one test per
+# point and repetition given outright, groups are of any size (some empty),
+# and the count, CSR and Alg. 3 steps must still follow their definitions.
+
+def test_design_groups_by_hand():
+    g = np.array([[2, 0, 2, 2], [1, 1, 0, 1]], np.uint16)      # R = 2, n = 4, B = 3
+    gid = O.design_groups(g, B=3)
+    assert gid.tolist() == [[2, 1], [0, 1], [2, 0], [2, 1]]
+    moff, mem = O.members(gid, 3)
+    # repetition 0: group 0 = {1}, group 1 = {}, group 2 = {0, 2, 3}
+    assert moff[0].tolist() == [0, 1, 1, 4] and mem[0, :4].tolist() == [1, 0, 2, 3]
+    with pytest.raises(ValueError):
+        O.design_groups(np.array([[0, 3]], np.uint16), B=3)
+
+
+def test_design_equal_to_alg1_gives_the_same_index():
+    # Alg. 1's own groups, given outright, rebuild the permutation's index
+    idx, pts = _dense_index(6, 300, 16, 3, 20, 8, 6)
+    perm_gid = idx.gid
+    jdx = O.OracleIndex("cosine", 3, 20, 8, 6, 6, srp_w=idx.srp_w)
+    jdx.build_groups(pts, perm_gid.T)
+    assert np.array_equal(jdx.off, idx.off) and np.array_equal(jdx.cells, idx.cells)
+    q = pts[::13]
+    assert all(np.array_equal(a, b) for a, b in zip(jdx.query(q, 20), idx.query(q, 20)))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_irregular_design_counts_equal_brute_force(seed):
+    N, L, R, B, W = 150, 6, 3, 12, 3
+    rng = np.random.default_rng(200 + seed)
+    buckets = rng.integers(0, 1 << W, size=(N, L), dtype=np.uint64).astype(np.uint32)
+    gid = O.design_groups(WL.random_design(seed, R, N, B), B)
+    assert np.any(np.bincount(gid[:, 0], minlength=B) != N // B)   # not doubly regular
+    off, cells = O.build_csr(buckets, gid, B, W)
+    q = rng.integers(0, 1 << W, size=L).astype(np.uint32)
+    cnt = O.counts(off, cells, L, W, q, B * R)
+    brute = np.zeros(B * R, np.int64)
+    for r in range(R):
+        for b in range(B):
+            mem = np.nonzero(gid[:, r] == b)[0]
+            for l in range(L):
+                brute[r * B + b] += bool(np.any(buckets[mem, l] == q[l]))
+    assert np.array_equal(cnt.astype(np.int64), brute)
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_irregular_design_alg3_equals_closed_key(seed):
+    rng = np.random.default_rng(500 + seed)
+    N = int(rng.integers(1, 65))
+    R = int(rng.integers(1, 5))
+    B = int(rng.integers(1, N + 3))            # B may exceed N: empty groups
+    L = int(rng.integers(1, 9))
+    if seed % 5 == 0:
+        g = np.zeros((R, N), np.uint16)        # every point in one group
+    else:
+        g = WL.random_design(seed, R, N, B)
+    gid = O.design_groups(g, B)
+    moff, mem = O.members(gid, B)
+    cnt = rng.integers(0, L + 1, size=B * R).astype(np.uint8)
+    for k in (1, 3, N, N + 5):
+        for t_min in (1, 2, L):
+            ids, sc, n = O.alg3(cnt, moff, mem, N, R, B, k=k, t_min=t_min)
+            e_ids, e_sc = closed_key_order(cnt, gid, B, k, t_min)
+            assert ids[:n].tolist() == e_ids and sc[:n].tolist() == e_sc
+            assert np.all(ids[n:] == 0xFFFFFFFF)
+
+
+def test_insert_groups_equals_build_of_union():
+    pts, _ = WL.gaussian_mixture(8, 500, 12, 10, 0.1)
+    w = WL.srp_projections(8, 5 * 7, 12)
+    g = WL.random_design(8, 2, 500, 25)
+    a = O.OracleIndex("cosine", 2, 25, 5, 7, 7, srp_w=w)
+    a.build_groups(pts, g)
+    b = O.OracleIndex("cosine", 2, 25, 5, 7, 7, srp_w=w)
+    b.build_groups(pts[:200], g[:, :200])
+    b.insert_groups(pts[200:], g[:, 200:])
+    assert np.array_equal(a.off, b.off) and np.array_equal(a.cells, b.cells)
+    assert np.array_equal(a.moff, b.moff) and np.array_equal(a.mem, b.mem)
