@@ -29,6 +29,10 @@
  *    in place, and reads the queries in place where it loads each element
  *    once (Jaccard queries; cosine queries hashed per CTA, see
  *    flinng_set_query_mode).
+ *  - Threads: calls on one index must not overlap; the caller serialises
+ *    them (an index owns one stream, one workspace and its CUDA graphs).
+ *    Different indices may be used from different threads at once, except
+ *    for flinng_query_noalloc, whose calls all share one scratch array.
  *  - Point ids are insertion order: the first build gives ids 0..n-1, each
  *    insert continues the numbering.
  *  - Cell ids are r * B + b for repetition r and group b; they are 16-bit
