@@ -290,34 +290,52 @@ class Index:
         fp.off, fp.elems = off.ctypes.data, el.ctypes.data
         return fp, off.shape[0] - 1, 0, [off, el]
 
+    def _rows(self, a, n: int, dt, name: str, dev: int):
+        """An R x n array of dt (host) or a contiguous R x n tensor of the same
+        element size (device), on the same side as the call's other buffers:
+        the library reads exactly R * n entries there."""
+        if bool(_is_cuda(a)) != bool(dev):
+            raise ValueError(f"{name} must live where the points do (host or device)")
+        if _is_cuda(a):
+            import torch
+            want = {np.uint32: (torch.int32,), np.uint16: (torch.int16,) + ((torch.uint16,) if hasattr(torch, "uint16")
+                                                                           else ())}[dt]
+            if a.dtype not in want or not a.is_contiguous() or tuple(a.shape) != (self.R, n):
+                raise ValueError(f"{name} must be a contiguous {self.R} x {n} tensor of {want[0]}")
+            return a
+        a = _np(a, dt)
+        if a.shape != (self.R, n):
+            raise ValueError(f"{name} must be {self.R} x {n}")
+        return a
+
     def build(self, pts, perm):
         fp, n, dev, keep = self._points(pts)
-        perm = perm if _is_cuda(perm) else _np(perm, np.uint32)
+        perm = self._rows(perm, n, np.uint32, "perm", dev)
         _check(self.lib.flinng_build(self.h, C.byref(fp), n, _ptr(perm), dev))
 
     def build_buckets(self, buckets, perm):
         """Build from precomputed buckets (n x L)."""
         dev = int(_is_cuda(buckets))
         b = buckets if dev else _np(buckets, np.uint32)
-        perm = perm if _is_cuda(perm) else _np(perm, np.uint32)
+        perm = self._rows(perm, b.shape[0], np.uint32, "perm", dev)
         _check(self.lib.flinng_build_buckets(self.h, _ptr(b), b.shape[0], _ptr(perm), dev))
 
     def insert(self, pts, perm):
         fp, n, dev, keep = self._points(pts)
-        perm = perm if _is_cuda(perm) else _np(perm, np.uint32)
+        perm = self._rows(perm, n, np.uint32, "perm", dev)
         _check(self.lib.flinng_insert(self.h, C.byref(fp), n, _ptr(perm), dev))
 
     def build_groups(self, pts, groups):
         """Build with the design given outright: groups (R x n uint16), row r
         holding each point's group in repetition r."""
         fp, n, dev, keep = self._points(pts)
-        g = groups if _is_cuda(groups) else _np(groups, np.uint16)
+        g = self._rows(groups, n, np.uint16, "groups", dev)
         _check(self.lib.flinng_build_groups(self.h, C.byref(fp), n, _ptr(g), dev))
 
     def insert_groups(self, pts, groups):
         """Insert with the new points' groups given (R x n uint16)."""
         fp, n, dev, keep = self._points(pts)
-        g = groups if _is_cuda(groups) else _np(groups, np.uint16)
+        g = self._rows(groups, n, np.uint16, "groups", dev)
         _check(self.lib.flinng_insert_groups(self.h, C.byref(fp), n, _ptr(g), dev))
 
     def _out(self, dev, shape, dt):
@@ -355,6 +373,11 @@ class Index:
             if not dev and (ids.dtype != np.uint32 or sc.dtype != np.uint16 or not ids.flags.c_contiguous
                             or not sc.flags.c_contiguous):
                 raise ValueError("host out buffers must be C-contiguous uint32 and uint16 arrays")
+            if dev:
+                import torch
+                if (ids.dtype != torch.int32 or sc.dtype != torch.int16 or not ids.is_contiguous()
+                        or not sc.is_contiguous()):
+                    raise ValueError("device out buffers must be contiguous int32 and int16 tensors")
         kk = None if k is None else (k if _is_cuda(k) else _np(k, np.uint32))
         _check(self.lib.flinng_query(self.h, C.byref(fp), nq, _ptr(kk), k_max, _ptr(ids), _ptr(sc), dev))
         return ids, sc

@@ -115,7 +115,7 @@ def test_embeddings_full_size_sampled(F):
         fp = F.flinng_points()
         fp.x, fp.ld = x.data_ptr(), d
         F._check(ix.lib.flinng_hash(ix.h, C.byref(fp), n, all_b[first:first + n].data_ptr(), None, None, 1))
-    ix.build_buckets(all_b, perm)
+    ix.build_buckets(all_b, torch.from_numpy(perm.view(np.int32)).cuda())
     codes = all_b.cpu().numpy().view(np.uint32)
     samp = np.unique(np.concatenate([[0, N - 1], np.random.default_rng(3).choice(N, 94, replace=False)]))
     assert np.array_equal(codes[samp], O.srp_codes(WL.embed_points(seed, samp, d, nc, sig), w, L, K))

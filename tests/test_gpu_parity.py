@@ -465,6 +465,15 @@ def test_pinned_host_buffers_in_place(F):
         assert np.array_equal(ids, cid) and np.array_equal(sc, csc), mode
     with pytest.raises(ValueError):
         jx.query(pqd, 12, out=(ci[:, :5], cs))
+    # device queries: the out tensors' dtype and layout are checked before any launch
+    import torch
+    dq = torch.from_numpy(qd).cuda()
+    for bad in [(torch.empty((150, 12), dtype=torch.int16, device="cuda"),
+                 torch.empty((150, 12), dtype=torch.int16, device="cuda")),
+                (torch.empty((12, 150), dtype=torch.int32, device="cuda").t(),
+                 torch.empty((150, 12), dtype=torch.int16, device="cuda"))]:
+        with pytest.raises(ValueError):
+            jx.query(dq, 12, out=bad)
 
 
 def test_graph_mode_cosine_stats_reset(F):
