@@ -1,0 +1,148 @@
+"""CPU models of two pieces of the query kernels' arithmetic, checked against
+their plain definitions (no GPU).
+
+* Heavy-bucket counts (Sec. 5: a cell's count is the number of tables whose
+  bucket holds it). For a heavy bucket the kernels add the cell bitmaps of
+  all heavy tables in bit-sliced form: a carry-save adder tree over eight
+  bitmap words, the weight-8 carry rippled into higher planes, a pass per
+  248 tables, then the planes spread into packed 8- or 16-bit counters. The
+  model must give each cell's number of set bits, for any table count.
+* The contiguous-slice walk over flattened lists. Each warp takes a slice of
+  the entries; a lane finds its list by a forward search from its previous
+  one (four steps, then a binary search), ended by the prefix sums past the
+  last list and a sentinel at NT. The model must visit every entry exactly
+  once, in its own list, with empty lists anywhere.
+"""
+import numpy as np
+import pytest
+
+M32 = 0xFFFFFFFF
+
+
+def csa(a, b, c):
+    u = a ^ b
+    return (a & b) | (u & c), u ^ c            # carry, sum
+
+
+def bitsliced_counts(words, cw):
+    """words: (nh, nw) uint32 bitmaps. Returns the packed counter words the
+    kernels add: cw = 1 -> 8 words of 4 byte counts per bitmap word, cw = 2
+    -> 16 words of 2 half-word counts."""
+    nh, nw = words.shape
+    k_per = 8 if cw == 1 else 16
+    k_cells = 32 // k_per
+    out = np.zeros(nw * k_per, np.uint64)
+    for w in range(nw):
+        for i1 in range(0, nh, 248):
+            i2 = min(nh, i1 + 248)
+            pl = [0] * 8
+            for i0 in range(i1, i2, 8):
+                x = [int(words[i0 + v, w]) if i0 + v < i2 else 0 for v in range(8)]
+                t0, pl[0] = csa(pl[0], x[0], x[1])
+                t1, pl[0] = csa(pl[0], x[2], x[3])
+                f0, pl[1] = csa(pl[1], t0, t1)
+                t0, pl[0] = csa(pl[0], x[4], x[5])
+                t1, pl[0] = csa(pl[0], x[6], x[7])
+                f1, pl[1] = csa(pl[1], t0, t1)
+                e, pl[2] = csa(pl[2], f0, f1)
+                for p in range(3, 8):
+                    c = pl[p] & e
+                    pl[p] ^= e
+                    e = c
+                assert e == 0                      # at most 247 per pass: 8 planes suffice
+            np_ = (i2 - i1).bit_length()
+            for j in range(k_per):
+                acc = 0
+                for p in range(np_):
+                    bits = (pl[p] >> (k_cells * j)) & ((1 << k_cells) - 1)
+                    if cw == 1:
+                        acc += ((bits * 0x00204081) & 0x01010101) << p
+                    else:
+                        acc += ((bits * 0x8001) & 0x10001) << p
+                out[w * k_per + j] += acc & M32
+    return out
+
+
+@pytest.mark.parametrize("nh", [1, 2, 7, 8, 9, 63, 247, 248, 249, 255, 500, 1000])
+@pytest.mark.parametrize("cw", [1, 2])
+def test_bitsliced_heavy_counts_equal_popcounts(nh, cw):
+    if cw == 1 and nh > 255:
+        pytest.skip("8-bit counters hold at most 255 tables")
+    rng = np.random.default_rng([nh, cw])
+    nw = 3
+    words = rng.integers(0, 1 << 32, size=(nh, nw), dtype=np.uint64).astype(np.uint32)
+    if nh > 5:
+        words[:, 0] = M32                      # every table holds the first word's cells
+        words[: nh // 2, 1] = 0
+    got = bitsliced_counts(words, cw)
+    k_per = 8 if cw == 1 else 16
+    k_cells = 32 // k_per
+    width = 8 if cw == 1 else 16
+    for w in range(nw):
+        for cell in range(32):
+            want = int(((words[:, w].astype(np.uint64) >> cell) & 1).sum())
+            j, i = divmod(cell, k_cells)
+            field = (int(got[w * k_per + j]) >> (width * i)) & ((1 << width) - 1)
+            assert field == want, (w, cell)
+
+
+def find_seg(pre, n, j, lo=0):
+    hi = n
+    while hi - lo > 1:
+        mid = (lo + hi) >> 1
+        if pre[mid] <= j:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+def slice_walk(lens, NT, U):
+    """Entries visited by the kernels' contiguous-slice walk: (entry, list)."""
+    n = len(lens)
+    assert n <= NT
+    pre = np.zeros(NT + 1, np.int64)
+    total = int(sum(lens))
+    run = 0
+    for t in range(NT):
+        pre[t] = run
+        run += lens[t] if t < n else 0
+    pre[NT] = M32                               # the sentinel
+    seen = []
+    nwarps = NT // 32
+    per = ((total + nwarps - 1) // nwarps + 31) & ~31
+    for w in range(nwarps):
+        eb0 = min(w * per, total)
+        ee = min(eb0 + per, total)
+        for lane in range(32):
+            hint = [find_seg(pre, n, eb0 + u * 32 + lane) if eb0 + u * 32 + lane < ee else 0 for u in range(U)]
+            for eb in range(eb0, ee, 32 * U):
+                for u in range(U):
+                    e = eb + u * 32 + lane
+                    if e >= ee:
+                        continue
+                    t = hint[u]
+                    step = 0
+                    while pre[t + 1] <= e:
+                        if step == 4:
+                            t = find_seg(pre, n, e, t + 1)
+                            break
+                        t += 1
+                        step += 1
+                    hint[u] = t
+                    seen.append((e, t))
+    return seen, pre
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_slice_walk_visits_every_entry_once_in_its_list(seed):
+    rng = np.random.default_rng(seed)
+    NT = int(rng.choice([128, 256, 512]))
+    U = int(rng.choice([1, 4]))
+    n = int(rng.integers(1, NT + 1))
+    lens = rng.choice([0, 0, 1, 3, 17, 40, 200, 1000], size=n).tolist()
+    seen, pre = slice_walk(lens, NT, U)
+    total = int(sum(lens))
+    assert sorted(e for e, _ in seen) == list(range(total))
+    for e, t in seen:
+        assert pre[t] <= e < pre[t] + lens[t] and lens[t] > 0
