@@ -264,7 +264,8 @@ int flinng_set_tuning(flinng_index *idx, uint32_t nq, uint32_t threads, uint32_t
 
 /*
  * Hash n points with the index's LSH functions (Sec. 3.2 concatenation,
- * Sec. 5 shared functions).
+ * Sec. 5 shared functions). Errors: INVALID_ARG (null buckets, malformed
+ * points), TIMEOUT (tensor-core precision: a bounded wait gave up), CUDA.
  * out_buckets: n x L uint32 bucket per table (SRP: the K sign bits, bit j =
  *   (projection l*K + j > 0); Jaccard: the W-bit combination of the K MinHash
  *   values of table l).
@@ -278,7 +279,10 @@ int flinng_hash(flinng_index *idx, const flinng_points *pts, uint64_t n,
 
 /*
  * Query from precomputed buckets (nq x L), skipping the hash step.
- * Same outputs as flinng_query.
+ * Same outputs as flinng_query. Every bucket must be < 2^W: host buffers are
+ * checked (INVALID_ARG, nothing launched); device buffers are not checked,
+ * and keeping them in range is the caller's part of the contract.
+ * Errors: as flinng_query.
  */
 int flinng_query_buckets(flinng_index *idx, const uint32_t *qbuckets,
                          uint32_t nq, const uint32_t *k, uint32_t k_max,
@@ -287,7 +291,8 @@ int flinng_query_buckets(flinng_index *idx, const uint32_t *qbuckets,
 
 /*
  * Per-cell collision counts of nq queries given their buckets (Sec. 5):
- * out_counts nq x (B*R) uint16 (each in 0..L).
+ * out_counts nq x (B*R) uint16 (each in 0..L). Buckets < 2^W, checked as in
+ * flinng_query_buckets. Errors: INVALID_ARG, CUDA.
  */
 int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq,
                   uint16_t *out_counts, int on_device);

@@ -690,10 +690,22 @@ int flinng_query(flinng_index *idx, const flinng_points *q, uint32_t nq, const u
     return query_common(idx, q, nullptr, nq, k, k_max, out_ids, out_scores, on_device);
 }
 
+// Host buckets are checked against 2^W before any copy (the kernels index the
+// table's slots with them); device buckets are the caller's to keep in range.
+static int check_host_buckets(const flinng_index *idx, const uint32_t *qb, uint64_t n, const char *what)
+{
+    const uint32_t W = idx->cfg.range_bits;
+    for (uint64_t i = 0; i < n; ++i)
+        if (qb[i] >> W) return set_error(FLINNG_ERR_INVALID_ARG, "%s: a bucket is >= 2^W", what);
+    return FLINNG_OK;
+}
+
 int flinng_query_buckets(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq, const uint32_t *k,
                          uint32_t k_max, uint32_t *out_ids, uint16_t *out_scores, int on_device)
 {
     if (nq > 0 && !qbuckets) return set_error(FLINNG_ERR_INVALID_ARG, "query: qbuckets is null");
+    if (idx && nq > 0 && !on_device)
+        FL_TRY(check_host_buckets(idx, qbuckets, uint64_t(nq) * idx->cfg.L, "query_buckets"));
     return query_common(idx, nullptr, qbuckets, nq, k, k_max, out_ids, out_scores, on_device);
 }
 
@@ -746,6 +758,7 @@ int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq, uint
     const cudaStream_t st = idx->stream;
     const uint32_t L = idx->cfg.L, BR = idx->BR;
     if (on_device) return counts_launch(idx, qbuckets, nq, out_counts);
+    FL_TRY(check_host_buckets(idx, qbuckets, uint64_t(nq) * L, "counts"));
     FL_TRY(ws_reserve(idx, carve_bytes<uint32_t>(uint64_t(nq) * L) + carve_bytes<uint16_t>(uint64_t(nq) * BR) + 1024));
     Carver c(idx->ws.ptr, idx->ws.bytes);
     uint32_t *qb = c.take<uint32_t>(uint64_t(nq) * L);

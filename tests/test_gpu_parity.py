@@ -476,6 +476,23 @@ def test_pinned_host_buffers_in_place(F):
             jx.query(dq, 12, out=bad)
 
 
+def test_host_buckets_out_of_range_refused(F):
+    # a host bucket >= 2^W is refused before anything is copied or launched
+    pts, q, w, perm = dense_case(46, 300, 16, 10, 2, 10, 4, 6)
+    ix = F.Index("cosine", 2, 10, 4, 6, capacity=300, params=w, dim=16)
+    ix.build(pts, perm)
+    qb = O.srp_codes(q, w, 4, 6)
+    ids, sc = ix.query_buckets(qb, 5)
+    bad = qb.copy()
+    bad[3, 2] = 1 << 6
+    for call in (lambda: ix.query_buckets(bad, 5), lambda: ix.counts(bad)):
+        with pytest.raises(F.FlinngError) as e:
+            call()
+        assert e.value.code == F.ERR_INVALID_ARG
+    ids2, sc2 = ix.query_buckets(qb, 5)
+    assert np.array_equal(ids, ids2) and np.array_equal(sc, sc2)
+
+
 def test_graph_mode_cosine_stats_reset(F):
     pts, q, w, perm = dense_case(41, 800, 40, 50, 2, 20, 6, 7)
     q[0] = 0.0
