@@ -14,6 +14,7 @@
 // Bloom-filter bit is set once, Sec. 3.3) and the slots are compacted into
 // the final CSR.
 #include "internal.cuh"
+#include "trace.h"
 
 namespace flinng {
 
@@ -407,6 +408,7 @@ int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *per
     void *scan_ws = c.base + ((c.used + 255) & ~size_t(255));
 
     // groups of the new points: Alg. 1 from the permutations, or given outright
+    TraceRange stage1("groups and member lists");
     if (n > 0) {
         if (groups)
             k_groups_given<<<thread_blocks(uint64_t(R) * n), 256, 0, st>>>(groups, R, n, n_old, rp, ix->gid);
@@ -433,6 +435,8 @@ int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *per
         FL_CUDA(cudaGetLastError());
     }
 
+    stage1.end();
+    TraceRange stage2("reverse index");
     // reverse index: histogram of old lists + new entries per slot
     uint32_t *hist = ix->slot_a, *toff = ix->slot_b;
     const int have_old = (n_old > 0 && ix->n_cells > 0) ? 1 : 0;
@@ -475,6 +479,8 @@ int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *per
     FL_CUDA(cudaStreamSynchronize(st));
     ix->n_cells = *ix->h_flag;
     ix->n_points = N;
+    stage2.end();
+    TraceRange stage3("heavy bitmaps");
     FL_TRY(build_heavy(ix, scan_ws));
     return FLINNG_OK;
 }

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "trace.h"
 
 namespace flinng {
 
@@ -322,6 +323,7 @@ uint64_t flinng_kernel_launches(void) { return g_launches.load(); }
 int flinng_create(const flinng_config *cfg, const flinng_params *params, void *stream,
                   flinng_index **out)
 {
+    TraceRange trace_("flinng_create");
     if (!out) return set_error(FLINNG_ERR_INVALID_ARG, "create: out is null");
     *out = nullptr;
     FL_TRY(check_config(cfg, params));
@@ -441,6 +443,7 @@ int flinng_set_query_mode(flinng_index *idx, uint32_t mode)
 int flinng_tune_query(flinng_index *idx, const flinng_points *q, uint32_t nq, uint32_t k_max,
                       int on_device, uint32_t *chosen)
 {
+    TraceRange trace_("flinng_tune_query");
     if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
     if (nq == 0) return set_error(FLINNG_ERR_INVALID_ARG, "tune: empty batch");
     if (idx->cfg.metric == FLINNG_COSINE_SRP && uint64_t(idx->P) * idx->cfg.dim > (1ull << 18)) {
@@ -523,12 +526,14 @@ int flinng_set_tuning(flinng_index *idx, uint32_t nq, uint32_t threads, uint32_t
 int flinng_build(flinng_index *idx, const flinng_points *pts, uint64_t n, const uint32_t *perm,
                  int on_device)
 {
+    TraceRange trace_("flinng_build");
     return insert_common(idx, pts, n, perm, on_device, true);
 }
 
 int flinng_build_buckets(flinng_index *idx, const uint32_t *buckets, uint64_t n, const uint32_t *perm,
                          int on_device)
 {
+    TraceRange trace_("flinng_build_buckets");
     if (n > 0 && !buckets) return set_error(FLINNG_ERR_INVALID_ARG, "build_buckets: buckets is null");
     return insert_common(idx, nullptr, n, perm, on_device, true, buckets);
 }
@@ -536,12 +541,14 @@ int flinng_build_buckets(flinng_index *idx, const uint32_t *buckets, uint64_t n,
 int flinng_insert(flinng_index *idx, const flinng_points *pts, uint64_t n, const uint32_t *perm,
                   int on_device)
 {
+    TraceRange trace_("flinng_insert");
     return insert_common(idx, pts, n, perm, on_device, false);
 }
 
 int flinng_build_groups(flinng_index *idx, const flinng_points *pts, uint64_t n, const uint16_t *groups,
                         int on_device)
 {
+    TraceRange trace_("flinng_build_groups");
     if (n > 0 && !groups) return set_error(FLINNG_ERR_INVALID_ARG, "build_groups: groups is null");
     return insert_common(idx, pts, n, nullptr, on_device, true, nullptr, groups);
 }
@@ -549,6 +556,7 @@ int flinng_build_groups(flinng_index *idx, const flinng_points *pts, uint64_t n,
 int flinng_insert_groups(flinng_index *idx, const flinng_points *pts, uint64_t n, const uint16_t *groups,
                          int on_device)
 {
+    TraceRange trace_("flinng_insert_groups");
     if (n > 0 && !groups) return set_error(FLINNG_ERR_INVALID_ARG, "insert_groups: groups is null");
     return insert_common(idx, pts, n, nullptr, on_device, false, nullptr, groups);
 }
@@ -556,6 +564,7 @@ int flinng_insert_groups(flinng_index *idx, const flinng_points *pts, uint64_t n
 int flinng_hash(flinng_index *idx, const flinng_points *pts, uint64_t n, uint32_t *out_buckets,
                 uint32_t *out_values, float *out_proj, int on_device)
 {
+    TraceRange trace_("flinng_hash");
     if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
     if (n > 0 && !out_buckets) return set_error(FLINNG_ERR_INVALID_ARG, "hash: out_buckets is null");
     FL_TRY(check_points(idx, pts, n, on_device));
@@ -686,6 +695,7 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
 int flinng_query(flinng_index *idx, const flinng_points *q, uint32_t nq, const uint32_t *k,
                  uint32_t k_max, uint32_t *out_ids, uint16_t *out_scores, int on_device)
 {
+    TraceRange trace_("flinng_query");
     if (nq > 0 && !q) return set_error(FLINNG_ERR_INVALID_ARG, "query: q is null");
     return query_common(idx, q, nullptr, nq, k, k_max, out_ids, out_scores, on_device);
 }
@@ -703,6 +713,7 @@ static int check_host_buckets(const flinng_index *idx, const uint32_t *qb, uint6
 int flinng_query_buckets(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq, const uint32_t *k,
                          uint32_t k_max, uint32_t *out_ids, uint16_t *out_scores, int on_device)
 {
+    TraceRange trace_("flinng_query_buckets");
     if (nq > 0 && !qbuckets) return set_error(FLINNG_ERR_INVALID_ARG, "query: qbuckets is null");
     if (idx && nq > 0 && !on_device)
         FL_TRY(check_host_buckets(idx, qbuckets, uint64_t(nq) * idx->cfg.L, "query_buckets"));
@@ -712,6 +723,7 @@ int flinng_query_buckets(flinng_index *idx, const uint32_t *qbuckets, uint32_t n
 int flinng_query_counts(flinng_index *idx, const uint16_t *counts, uint32_t nq, uint32_t max_count,
                         const uint32_t *k, uint32_t k_max, uint32_t *out_ids, uint16_t *out_scores, int on_device)
 {
+    TraceRange trace_("flinng_query_counts");
     if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
     if (k_max > kMaxKMax) return set_error(FLINNG_ERR_INVALID_ARG, "query_counts: k_max > %u", kMaxKMax);
     if (max_count < 1 || max_count > kMaxL)
@@ -752,6 +764,7 @@ int flinng_query_counts(flinng_index *idx, const uint16_t *counts, uint32_t nq, 
 int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq, uint16_t *out_counts,
                   int on_device)
 {
+    TraceRange trace_("flinng_counts");
     if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
     if (nq == 0) return FLINNG_OK;
     if (!qbuckets || !out_counts) return set_error(FLINNG_ERR_INVALID_ARG, "counts: null buffer");
@@ -773,6 +786,7 @@ int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq, uint
 int flinng_export(flinng_index *idx, uint32_t *off, uint16_t *cells, uint64_t cells_cap,
                   uint64_t *n_cells, uint16_t *gid)
 {
+    TraceRange trace_("flinng_export");
     if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
     const cudaStream_t st = idx->stream;
     FL_CUDA(cudaStreamSynchronize(st));

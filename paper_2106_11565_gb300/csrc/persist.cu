@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "trace.h"
 
 using namespace flinng;
 
@@ -74,6 +75,7 @@ int read_host(FILE *f, std::vector<T> &v, uint64_t n)
 
 extern "C" int flinng_save(flinng_index *idx, const char *path)
 {
+    TraceRange trace_("flinng_save");
     if (!idx || !path) return set_error(FLINNG_ERR_INVALID_ARG, "save: null argument");
     const cudaStream_t st = idx->stream;
     FL_CUDA(cudaStreamSynchronize(st));
@@ -114,6 +116,7 @@ extern "C" int flinng_save(flinng_index *idx, const char *path)
 
 extern "C" int flinng_load(const char *path, void *stream, flinng_index **out)
 {
+    TraceRange trace_("flinng_load");
     if (!path || !out) return set_error(FLINNG_ERR_INVALID_ARG, "load: null argument");
     *out = nullptr;
     File fh;

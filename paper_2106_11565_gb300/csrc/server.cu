@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "trace.h"
 
 namespace flinng {
 namespace {
@@ -140,6 +141,7 @@ int size_slots(flinng_server *srv, size_t dbytes, size_t hbytes)
 // Launch the queries in slot.reqs against index si on the slot's stream.
 int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
 {
+    TraceRange trace_("server batch");
     ServerIndex &S = srv->idx[slot.index];
     flinng_index *ix = S.ix;
     const Layout Lo = layout_for(srv);
@@ -323,6 +325,7 @@ uint64_t flinng_server_device_bytes(const flinng_server *srv) { return srv ? srv
 int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_t n, uint32_t *out_ids,
                          uint16_t *out_scores, flinng_request_result *res)
 {
+    TraceRange trace_("flinng_server_replay");
     if (!srv || (n && (!reqs || !out_ids || !res))) return set_error(FLINNG_ERR_INVALID_ARG, "replay: null argument");
     const uint32_t km = srv->cfg.k_max;
     const Layout Lo = layout_for(srv);
