@@ -1,4 +1,4 @@
-"""CPU models of two pieces of the query kernels' arithmetic, checked against
+"""CPU models of three pieces of the query kernels' arithmetic, checked against
 their plain definitions (no GPU).
 
 * Heavy-bucket counts (Sec. 5: a cell's count is the number of tables whose
@@ -12,6 +12,9 @@ their plain definitions (no GPU).
   one (four steps, then a binary search), ended by the prefix sums past the
   last list and a sentinel at NT. The model must visit every entry exactly
   once, in its own list, with empty lists anywhere.
+* The radix select that cuts a buffer of more than 256 candidates to the k
+  best: the (prefix, mask) it returns must keep exactly the k smallest keys,
+  for 8- and 16-bit score fields and long runs of equal leading digits.
 """
 import numpy as np
 import pytest
@@ -146,3 +149,51 @@ def test_slice_walk_visits_every_entry_once_in_its_list(seed):
     assert sorted(e for e, _ in seen) == list(range(total))
     for e, t in seen:
         assert pre[t] <= e < pre[t] + lens[t] and lens[t] > 0
+
+
+# ---------------------------------------------------------------- radix select
+#
+# Buffers of more than 256 candidates are cut to the k best by a radix select
+# over the 64-bit keys (-score as kScoreMax - score, last cell, id): from the
+# top digit down, a histogram of the keys that match the prefix chosen so far
+# picks the digit holding the k-th key; it stops early once that digit's
+# bucket is taken whole. The kept keys are those with (key & mask) <= prefix.
+
+def block_select(keys, kk, top_shift):
+    prefix = mask = 0
+    rem = kk
+    for shift in range(top_shift, -1, -8):
+        hist = [0] * 256
+        for v in keys:
+            if (v & mask) == prefix:
+                hist[(v >> shift) & 0xFF] += 1
+        run, d = 0, 0
+        for d in range(256):
+            if run + hist[d] >= rem:
+                break
+            run += hist[d]
+        hd = hist[d]
+        rem -= run
+        prefix |= d << shift
+        mask |= 0xFF << shift
+        if hd == rem:
+            break
+    return prefix, mask
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_radix_select_keeps_exactly_the_k_smallest(seed):
+    rng = np.random.default_rng(seed)
+    wide = seed % 2 == 1                        # 16-bit counts: a 12-bit score field
+    kmax_score = 4095 if wide else 255
+    top_shift = 56 if wide else 48
+    n = int(rng.integers(257, 3000))
+    # few distinct scores and cells, so long runs of equal top digits
+    score = rng.integers(0, rng.choice([2, 5, kmax_score + 1]), size=n)
+    last = rng.integers(0, rng.choice([3, 60000]), size=n)
+    ids = rng.permutation(1 << 20)[:n]          # distinct ids: distinct keys
+    keys = [((kmax_score - int(s)) << 48) | (int(c) << 32) | int(x) for s, c, x in zip(score, last, ids)]
+    for kk in {1, 2, 10, 100, 256, n - 1, n, int(rng.integers(1, n + 1))}:
+        prefix, mask = block_select(keys, kk, top_shift)
+        kept = sorted(v for v in keys if (v & mask) <= prefix)
+        assert kept == sorted(keys)[:kk], kk
