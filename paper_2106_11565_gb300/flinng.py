@@ -141,6 +141,9 @@ def load(path: str | None = None):
 
 
 class FlinngError(RuntimeError):
+    """A failed library call: ``code`` is the FLINNG_ERR_* status, the
+    message the library's own."""
+
     def __init__(self, code: int, msg: str):
         super().__init__(f"[{code}] {msg}")
         self.code = code
@@ -253,6 +256,7 @@ class Index:
 
     # ---- lifecycle
     def close(self):
+        """Destroy the index and free its device memory (idempotent)."""
         if getattr(self, "h", None):
             self.lib.flinng_destroy(self.h)
             self.h = None
@@ -265,10 +269,12 @@ class Index:
 
     @property
     def size(self) -> int:
+        """Points in the index."""
         return int(self.lib.flinng_size(self.h))
 
     @property
     def device_bytes(self) -> int:
+        """Device memory the index holds."""
         return int(self.lib.flinng_device_bytes(self.h))
 
     # ---- points
@@ -309,6 +315,7 @@ class Index:
         return a
 
     def build(self, pts, perm):
+        """Build from scratch over pts with Alg. 1's permutations (R x n)."""
         fp, n, dev, keep = self._points(pts)
         perm = self._rows(perm, n, np.uint32, "perm", dev)
         _check(self.lib.flinng_build(self.h, C.byref(fp), n, _ptr(perm), dev))
@@ -321,6 +328,7 @@ class Index:
         _check(self.lib.flinng_build_buckets(self.h, _ptr(b), b.shape[0], _ptr(perm), dev))
 
     def insert(self, pts, perm):
+        """Add pts; perm (R x n) places them after the current points."""
         fp, n, dev, keep = self._points(pts)
         perm = self._rows(perm, n, np.uint32, "perm", dev)
         _check(self.lib.flinng_insert(self.h, C.byref(fp), n, _ptr(perm), dev))
@@ -347,6 +355,8 @@ class Index:
         return np.zeros(shape, dt)
 
     def hash(self, pts, values: bool = False, proj: bool = False):
+        """Buckets (n x L), and optionally MinHash values or projections
+        (n x L*K), of pts under the index's hash functions."""
         fp, n, dev, keep = self._points(pts)
         P = self.L * self.K
         b = self._out(dev, (n, self.L), np.uint32)
@@ -382,9 +392,20 @@ class Index:
         _check(self.lib.flinng_query(self.h, C.byref(fp), nq, _ptr(kk), k_max, _ptr(ids), _ptr(sc), dev))
         return ids, sc
 
+    def _table_rows(self, a, cols: int, dt, name: str):
+        """A 2-D array (host) or tensor (device) with cols columns: the
+        library reads exactly rows * cols entries."""
+        dev = int(_is_cuda(a))
+        a = a if dev else _np(a, dt)
+        if a.ndim != 2 or a.shape[1] != cols or (dev and not a.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous n x {cols} array")
+        if dev and a.element_size() != np.dtype(dt).itemsize:
+            raise ValueError(f"{name} must have {np.dtype(dt).itemsize}-byte elements")
+        return a, dev
+
     def query_buckets(self, qb, k_max: int, k=None):
-        dev = int(_is_cuda(qb))
-        qb = qb if dev else _np(qb, np.uint32)
+        """Top-k_max from query buckets (nq x L) instead of queries."""
+        qb, dev = self._table_rows(qb, self.L, np.uint32, "qbuckets")
         nq = qb.shape[0]
         ids = self._out(dev, (nq, k_max), np.uint32)
         sc = self._out(dev, (nq, k_max), np.uint16)
@@ -396,8 +417,7 @@ class Index:
     def query_counts(self, counts, k_max: int, max_count: int, k=None):
         """Decode from per-cell counts (nq x B*R, e.g. summed over table
         shards); max_count is the total table count."""
-        dev = int(_is_cuda(counts))
-        counts = counts if dev else _np(counts, np.uint16)
+        counts, dev = self._table_rows(counts, self.B * self.R, np.uint16, "counts")
         nq = counts.shape[0]
         ids = self._out(dev, (nq, k_max), np.uint32)
         sc = self._out(dev, (nq, k_max), np.uint16)
@@ -407,13 +427,14 @@ class Index:
         return ids, sc
 
     def counts(self, qb):
-        dev = int(_is_cuda(qb))
-        qb = qb if dev else _np(qb, np.uint32)
+        """Per-cell collision counts (nq x B*R) of query buckets (nq x L)."""
+        qb, dev = self._table_rows(qb, self.L, np.uint32, "qbuckets")
         out = self._out(dev, (qb.shape[0], self.B * self.R), np.uint16)
         _check(self.lib.flinng_counts(self.h, _ptr(qb), qb.shape[0], _ptr(out), dev))
         return out
 
     def export(self, cells: bool = True) -> dict:
+        """The index's CSR offsets, cell lists and group ids, on the host."""
         nc = C.c_uint64()
         _check(self.lib.flinng_export(self.h, None, None, 0, C.byref(nc), None))
         off = np.zeros((self.L << self.W) + 1, np.uint32)
@@ -424,6 +445,7 @@ class Index:
         return {"off": off, "cells": cl[: nc.value] if cells else None, "gid": gid[: self.size]}
 
     def set_query_mode(self, mode: int):
+        """QUERY_PLAIN, QUERY_FUSED or QUERY_GRAPH for flinng_query."""
         _check(self.lib.flinng_set_query_mode(self.h, mode))
 
     def tune(self, q, k_max: int) -> dict:
@@ -438,6 +460,7 @@ class Index:
         _check(self.lib.flinng_set_tuning(self.h, nq, threads, ctas_per_sm, cap))
 
     def hash_stats(self):
+        """(undecided, exact) projection counts of the last cosine hash."""
         a, b = C.c_uint64(), C.c_uint64()
         _check(self.lib.flinng_hash_stats(self.h, C.byref(a), C.byref(b)))
         return int(a.value), int(b.value)
@@ -479,6 +502,8 @@ class Server:
         self.h, self.k_max, self.indices = h, k_max, []
 
     def add_index(self, index: "Index") -> int:
+        """Make an index servable (admitted within the HBM budget); returns
+        its id for requests."""
         i = C.c_uint32()
         _check(self.lib.flinng_server_add_index(self.h, index.h, C.byref(i)))
         self.indices.append(index)
@@ -486,6 +511,7 @@ class Server:
 
     @property
     def device_bytes(self) -> int:
+        """Device memory the server's slots hold."""
         return int(self.lib.flinng_server_device_bytes(self.h))
 
     @property
@@ -514,6 +540,7 @@ class Server:
         return ids[:n], sc[:n], res
 
     def close(self):
+        """Destroy the server (its indices stay the caller's)."""
         if getattr(self, "h", None):
             self.lib.flinng_server_destroy(self.h)
             self.h = None
