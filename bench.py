@@ -218,8 +218,9 @@ def recall_scores(c: dict, got_ids: np.ndarray, exact_ids, exact_sims) -> dict:
 # --------------------------------------------------------------------------
 
 def query_kernel_bytes(c: dict, ex: dict, counts: np.ndarray, qb: np.ndarray, kq: int) -> dict:
-    """Per-launch algorithmic bytes of the query kernel, following its level
-    walk exactly: query buckets L*4, table offsets L*8; per table either its
+    """Per-launch algorithmic bytes of the query kernel, following Alg. 3's
+    level walk (the kernel walks whole level groups, so it may read more):
+    query buckets L*4, table offsets L*8; per table either its
     bucket list at 2 B a cell or, for a heavy slot (>= max(B*R/16, 32)
     cells, which the library stores as a bitmap over the B*R cells too), the
     bitmap's ceil(B*R/32)*4 B; then for every repetition-0 cell at count >= the
