@@ -364,10 +364,16 @@ uint64_t flinng_kernel_launches(void);
  * out_ids and out_scores are device memory; the call is asynchronous on the
  * index's stream. The index's device must be the current device.
  * Limits: nq * L <= 262144, and for cosine indices nq * L * K <= 655296.
- * Larger batches are rejected with FLINNG_ERR_INVALID_ARG (split them, or use
+ * Cosine indices of precision FLINNG_PREC_BF16X2 also stage the two bf16
+ * parts of every query row and two re-check lists in the same 5 MiB part of
+ * the array: about nq * (4 * dim + 16 * L * K + 4) + 8192 <= 5242880 bytes
+ * (the call computes the exact figure). Larger batches are rejected with
+ * FLINNG_ERR_INVALID_ARG before anything runs (split them, or use
  * flinng_query).
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The first call in a device's CUDA context looks up the scratch array's
+ * device address (cudaGetSymbolAddress) and caches it under that context's
+ * unique id; a context made again after cudaDeviceReset is looked up afresh.
+ * Make that first call before any stream capture.
  * All calls share the one array and it keeps the last call's contents (each
  * call overwrites what it reads): calls whose GPU work overlaps - on
  * different streams, or different indices - race on it and must be
@@ -416,11 +422,17 @@ typedef struct flinng_request {
 } flinng_request;
 
 typedef struct flinng_request_result {
-    double t_admit, t_start, t_done;   /* seconds after the start of the replay */
+    double t_admit, t_start, t_done;   /* host clock, seconds after the start of the replay:
+                                          admitted, batch launched (insert started), results
+                                          in the caller's buffers (insert done) */
     uint32_t status;           /* FLINNG_OK or the insert's error (CAPACITY, ...) */
     uint32_t version;          /* inserts applied to the index when the request ran */
     uint32_t batch;            /* queries: sequence number of the batch it ran in */
-    uint32_t reserved;
+    uint32_t slot;             /* queries: the stream slot (0..n_slots-1) the batch ran on */
+    double d_start, d_done;    /* queries: device clock (CUDA events on the slot's stream),
+                                  seconds after an event recorded when the replay began:
+                                  the batch's first copy started, its results reached the
+                                  host staging; 0 for inserts */
 } flinng_request_result;
 
 /* Create a server (streams and events; no index yet). */

@@ -465,8 +465,7 @@ int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *per
     // sort + dedupe each slot; ulen reuses the histogram buffer
     uint32_t *ulen = hist;
     const size_t smem = size_t(kWarpsPerBlock) * ((BR + 31) / 32) * sizeof(uint32_t);
-    if (smem > 48 * 1024)
-        FL_CUDA(cudaFuncSetAttribute(k_slot_unique, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FL_TRY(ensure_dyn_smem((const void *)k_slot_unique, smem));
     k_slot_unique<<<warp_blocks(nslot), kWarpsPerBlock * 32, smem, st>>>(toff, nslot, BR, ix->cells_tmp, ulen);
     count_launch();
     FL_CUDA(cudaGetLastError());

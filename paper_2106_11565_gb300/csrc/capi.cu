@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -32,6 +33,32 @@ int cuda_error(cudaError_t e, const char *what)
     const int code = (e == cudaErrorMemoryAllocation) ? FLINNG_ERR_OOM : FLINNG_ERR_CUDA;
     cudaGetLastError();   // clear a non-sticky error
     return set_error(code, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int ensure_dyn_smem(const void *fn, size_t smem)
+{
+    if (smem <= 48 * 1024) return FLINNG_OK;
+    struct Limit {
+        const void *fn;
+        int device;
+        size_t smem;
+    };
+    static std::mutex mu;
+    static std::vector<Limit> set;     // per kernel and device: the limit set so far
+    std::lock_guard<std::mutex> lock(mu);
+    int dev = 0;
+    FL_CUDA(cudaGetDevice(&dev));
+    for (Limit &e : set)
+        if (e.fn == fn && e.device == dev) {
+            if (e.smem < smem) {
+                FL_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                e.smem = smem;
+            }
+            return FLINNG_OK;
+        }
+    FL_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    set.push_back(Limit{fn, dev, smem});
+    return FLINNG_OK;
 }
 
 int ws_reserve(flinng_index *ix, size_t bytes)

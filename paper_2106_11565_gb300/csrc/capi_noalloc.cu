@@ -9,9 +9,14 @@
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds it (kScratchBytes) until the process exits. Host code cannot
-// use the variable's name as a device address; the address is looked up once
-// per device, with that device current, by cudaGetSymbolAddress, on the
-// first call made on that device.
+// use the variable's name as a device address; the address is looked up by
+// cudaGetSymbolAddress, with the device current, on the first call made in
+// each CUDA context of a device, and cached under that context's unique id.
+// A context torn down and made again (cudaDeviceReset, then any call) gets a
+// new id and a new module load, so the next call looks the address up again
+// instead of reusing a stale one.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "internal.cuh"
@@ -27,20 +32,55 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_query_scratch[kScratchBytes];
 
 std::mutex g_scratch_mu;
-void *g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+    unsigned long long ctx_id;   // unique id of the context the address belongs to (0: none yet)
+    void *ptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
 
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique id of the current context (ids are never reused within a process).
+int current_context_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        FL_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa));
+        FL_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb));
+        if (!a || !b || qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess)
+            return set_error(FLINNG_ERR_CUDA, "query_noalloc: cuCtxGetCurrent / cuCtxGetId not available");
+        get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+        get_id = reinterpret_cast<CtxGetIdFn>(b);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx)
+        return set_error(FLINNG_ERR_CUDA, "query_noalloc: no current CUDA context");
+    if (get_id(ctx, id) != CUDA_SUCCESS) return set_error(FLINNG_ERR_CUDA, "query_noalloc: cuCtxGetId failed");
+    return FLINNG_OK;
+}
+
+// Device address of the scratch array in the current context of `device`
+// (which must be the current device).
 int scratch_address(int device, void **out)
 {
     if (device < 0 || device >= kMaxDevices)
         return set_error(FLINNG_ERR_INVALID_ARG, "query_noalloc: device %d out of range", device);
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[device]) {
+    unsigned long long id = 0;
+    FL_TRY(current_context_id(&id));
+    ScratchAddr &a = g_scratch_addr[device];
+    if (a.ctx_id != id || !a.ptr) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_query_scratch);
         if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(query scratch)");
-        g_scratch_addr[device] = p;
+        a.ctx_id = id;
+        a.ptr = p;
     }
-    *out = g_scratch_addr[device];
+    *out = a.ptr;
     return FLINNG_OK;
 }
 
@@ -89,6 +129,8 @@ extern "C" int flinng_query_noalloc(flinng_index *idx, const flinng_points *q, u
     if (srp) {
         FL_TRY(srp_hash(idx, q->x, q->ld, nq, qb, nullptr, hws, kHashBytes));
     } else {
+        // the same counters as flinng_query leaves (zero for MinHash)
+        FL_CUDA(cudaMemsetAsync(idx->stats, 0, kStats * sizeof(unsigned long long), idx->stream));
         FL_TRY(doph_hash(idx, q->off, q->elems, nq, qb, nullptr));
     }
     return query_launch(idx, qb, nq, k, k_max, out_ids, out_scores);

@@ -335,8 +335,7 @@ int doph_hash(flinng_index *ix, const uint64_t *off, const uint32_t *elems,
     if (n == 0) return FLINNG_OK;
     const uint32_t nb = ix->P;
     const size_t smem = size_t(kDophWarps) * (nb + (nb + 31) / 32) * sizeof(uint32_t);
-    if (smem > 48 * 1024)
-        FL_CUDA(cudaFuncSetAttribute(k_doph, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FL_TRY(ensure_dyn_smem((const void *)k_doph, smem));
     uint64_t blocks = (n + kDophWarps - 1) / kDophWarps;
     if (blocks > 152ull * 64) blocks = 152ull * 64;
     k_doph<<<(unsigned)blocks, kDophWarps * 32, smem, ix->stream>>>(

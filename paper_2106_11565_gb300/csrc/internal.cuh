@@ -54,6 +54,15 @@ struct QueryTuning {
     uint32_t valid;
 };
 
+// Occupancy of one fused-kernel launch shape, kept per index so that a
+// launch does not query it again.
+struct OccEntry {
+    const void *fn;
+    int threads;
+    size_t smem;
+    int per_sm;
+};
+
 struct QueryGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -135,6 +144,9 @@ struct flinng_index {
     flinng::Workspace ws;
     uint64_t device_bytes;
     uint32_t query_mode;   // FLINNG_QUERY_PLAIN, _FUSED or _GRAPH
+    int sms;               // multiprocessors of the device (0: not looked up yet)
+    flinng::OccEntry occ[8];          // occupancy of recent fused launch shapes
+    uint32_t n_occ;
     flinng::QueryTuning tuning[33];   // per batch-size class (ceil log2 nq)
     flinng::QueryGraph graphs[33];
 };
@@ -142,6 +154,10 @@ struct flinng_index {
 namespace flinng {
 
 int ws_reserve(flinng_index *ix, size_t bytes);
+
+// Raise a kernel's dynamic shared-memory limit to at least `smem` (never
+// lowers it, so launches from other indices keep their headroom).
+int ensure_dyn_smem(const void *fn, size_t smem);
 
 // Process-wide count of kernel launches made by the library.
 void count_launch(unsigned n = 1);

@@ -99,8 +99,7 @@ int query_launch_counts(flinng_index *ix, const uint32_t *qbuckets, const uint16
                          "query: k_max=%u with B*R=%u needs %zu bytes of shared memory (> 227 KB)",
                          k_max, a.BR, smem);
     const void *fn = cw == 1 ? plain_kernel_c1(NT, ix->rw) : plain_kernel_c2(NT, ix->rw);
-    if (smem > 48 * 1024)
-        FL_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FL_TRY(ensure_dyn_smem(fn, smem));
     void *args[] = {&a};
     FL_CUDA(cudaLaunchKernel(fn, dim3(nq), dim3(NT), args, smem, ix->stream));   // one CTA per query
     count_launch();
@@ -167,13 +166,20 @@ static int fused_prepare(flinng_index *ix, const FusedQuery &fq, const uint32_t 
         return set_error(FLINNG_ERR_INVALID_ARG, "fused query: %zu bytes of shared memory needed (> 227 KB)", P->smem);
     P->fn = ix->cw == 1 ? fused_kernel_c1(NT, ix->rw, srp) : fused_kernel_c2(NT, ix->rw, srp);
     P->threads = NT;
-    if (P->smem > 48 * 1024)
-        FL_CUDA(cudaFuncSetAttribute(P->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem));
+    FL_TRY(ensure_dyn_smem(P->fn, P->smem));
     int per_sm = 0;
-    FL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P->fn, NT, P->smem));
-    if (per_sm < 1) per_sm = 1;
-    int sms = 0;
-    FL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device));
+    for (uint32_t i = 0; i < ix->n_occ; ++i) {
+        const OccEntry &e = ix->occ[i];
+        if (e.fn == P->fn && e.threads == NT && e.smem == P->smem) per_sm = e.per_sm;
+    }
+    if (!per_sm) {
+        FL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P->fn, NT, P->smem));
+        if (per_sm < 1) per_sm = 1;
+        const uint32_t slot = ix->n_occ < 8 ? ix->n_occ++ : 7;
+        ix->occ[slot] = OccEntry{P->fn, NT, P->smem, per_sm};
+    }
+    if (!ix->sms) FL_CUDA(cudaDeviceGetAttribute(&ix->sms, cudaDevAttrMultiProcessorCount, ix->device));
+    const int sms = ix->sms;
     uint32_t want = (tune && tune->ctas_per_sm) ? tune->ctas_per_sm : uint32_t(per_sm);
     if (want > uint32_t(per_sm)) want = per_sm;
     uint64_t grid = uint64_t(sms) * want;
@@ -269,8 +275,7 @@ int counts_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
     a.out_counts = out_counts;
     const size_t smem = qsmem_bytes(a.cap, a.kp, a.BR, a.B, kQTmax, a.L, int(ix->cw));
     const void *fn = ix->cw == 1 ? counts_kernel_c1() : counts_kernel_c2();
-    if (smem > 48 * 1024)
-        FL_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FL_TRY(ensure_dyn_smem(fn, smem));
     void *args[] = {&a};
     FL_CUDA(cudaLaunchKernel(fn, dim3(nq), dim3(kQTmax), args, smem, ix->stream));
     count_launch();

@@ -33,7 +33,8 @@ namespace {
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr;   // recorded before the batch's first copy (timing)
+    cudaEvent_t done = nullptr;    // recorded after its results reach the host staging (timing)
     bool busy = false;
     uint32_t index = 0;
     std::vector<uint64_t> reqs;
@@ -52,10 +53,18 @@ struct ServerIndex {
     std::deque<uint64_t> pending;
 };
 
-// Per-slot layout (device and host mirror): counter + stats, per-query k,
-// query input (rows or CSR), query buckets, re-check list, outputs.
+// Per-slot layout (device and host mirror): counter + stats, the batch
+// header (gather descriptors, input offsets, per-query k: one copy), query
+// input (rows or CSR), query buckets, re-check list, outputs.
 struct Layout {
-    size_t k, in_off, in_el, qb, srp, ids, sc, desc, total;
+    size_t hdr, in_el, qb, srp, ids, sc, total;
+};
+
+// Offsets inside the header region for a batch of nb queries: descriptors,
+// then nb + 1 input offsets, then nb values of k; `bytes` is what one copy
+// moves to the device.
+struct HdrOff {
+    size_t desc, in_off, k, bytes;
 };
 
 // One request's input for the device gather: 4-byte words from a host
@@ -87,6 +96,7 @@ struct flinng_server {
     uint32_t max_L = 0, max_dim = 0;
     uint64_t max_P = 0;
     bool device_gather = false;   // the GPU reads requests' host buffers directly
+    cudaEvent_t ref = nullptr;    // recorded when a replay begins: origin of the device times
 };
 
 namespace flinng {
@@ -98,23 +108,32 @@ double now_s()
     return std::chrono::duration<double>(C::now().time_since_epoch()).count();
 }
 
+HdrOff hdr_for(uint64_t nb)
+{
+    Carver c(nullptr, ~size_t(0));
+    HdrOff h{};
+    h.desc = (size_t)c.take<GatherDesc>(nb);
+    h.in_off = (size_t)c.take<uint64_t>(nb + 1);
+    h.k = (size_t)c.take<uint32_t>(nb);
+    h.bytes = c.used;
+    return h;
+}
+
 Layout layout_for(const flinng_server *srv)
 {
     const uint64_t nb = srv->cfg.max_batch, km = srv->cfg.k_max;
     Layout L{};
     Carver c(nullptr, ~size_t(0));
     c.take<unsigned long long>(8);                                  // query counter, 4 hash counters
-    L.k = (size_t)c.take<uint32_t>(nb);
+    L.hdr = (size_t)c.take<char>(hdr_for(nb).bytes);
     const uint64_t in_floats = nb * uint64_t(srv->max_dim);
     const uint64_t in_elems = uint64_t(srv->cfg.max_batch_elems);
-    L.in_off = (size_t)c.take<uint64_t>(nb + 1);
     L.in_el = (size_t)c.take<uint32_t>(in_floats > in_elems ? in_floats : in_elems);
     L.qb = (size_t)c.take<uint32_t>(nb * srv->max_L);
     // re-check lists (fp32 path) or the tensor-core split operands and lists
     L.srp = (size_t)c.take<unsigned long long>(2 * nb * srv->max_P + 64 + nb * srv->max_dim / 2 + nb + 1024);
     L.ids = (size_t)c.take<uint32_t>(nb * km);
     L.sc = (size_t)c.take<uint16_t>(nb * km);
-    L.desc = (size_t)c.take<GatherDesc>(nb);
     L.total = c.used + 256;
     return L;
 }
@@ -150,13 +169,16 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
     const bool srp = ix->cfg.metric == FLINNG_COSINE_SRP;
     char *h = static_cast<char *>(slot.hstage);
     char *d = static_cast<char *>(slot.dscratch);
-    uint32_t *hk = reinterpret_cast<uint32_t *>(h + Lo.k);
-    size_t in_bytes;
+    const HdrOff ho_ = hdr_for(nb);
+    char *hh = h + Lo.hdr;
+    char *dh = d + Lo.hdr;
+    uint32_t *hk = reinterpret_cast<uint32_t *>(hh + ho_.k);
+    uint64_t *ho = reinterpret_cast<uint64_t *>(hh + ho_.in_off);
+    FL_CUDA(cudaEventRecord(slot.start, slot.stream));
+    ho[0] = 0;
     if (srv->device_gather) {
         // descriptors only: the gather kernel reads each request's buffer
-        GatherDesc *hd = reinterpret_cast<GatherDesc *>(h + Lo.desc);
-        uint64_t *ho = reinterpret_cast<uint64_t *>(h + Lo.in_off);
-        ho[0] = 0;
+        GatherDesc *hd = reinterpret_cast<GatherDesc *>(hh + ho_.desc);
         for (uint32_t i = 0; i < nb; ++i) {
             const flinng_request &r = reqs[slot.reqs[i]];
             hk[i] = r.k;
@@ -164,41 +186,34 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
             hd[i] = GatherDesc{reinterpret_cast<uint64_t>(r.data), ho[i], r.data ? n : 0};
             ho[i + 1] = ho[i] + n;
         }
-        FL_CUDA(cudaMemcpyAsync(d + Lo.k, h + Lo.k, nb * sizeof(uint32_t), cudaMemcpyHostToDevice, slot.stream));
-        if (!srp)
-            FL_CUDA(cudaMemcpyAsync(d + Lo.in_off, h + Lo.in_off, (nb + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice,
-                                    slot.stream));
-        FL_CUDA(cudaMemcpyAsync(d + Lo.desc, h + Lo.desc, nb * sizeof(GatherDesc), cudaMemcpyHostToDevice,
-                                slot.stream));
+        // header (descriptors, offsets, k) in one copy
+        FL_CUDA(cudaMemcpyAsync(dh, hh, ho_.bytes, cudaMemcpyHostToDevice, slot.stream));
         const unsigned grid = nb < 152u * 8u ? nb : 152u * 8u;
-        k_gather_requests<<<grid, 256, 0, slot.stream>>>(reinterpret_cast<const GatherDesc *>(d + Lo.desc), nb,
+        k_gather_requests<<<grid, 256, 0, slot.stream>>>(reinterpret_cast<const GatherDesc *>(dh + ho_.desc), nb,
                                                           reinterpret_cast<uint32_t *>(d + Lo.in_el));
         count_launch();
         FL_CUDA(cudaGetLastError());
-    } else if (srp) {
-        float *hx = reinterpret_cast<float *>(h + Lo.in_el);
-        for (uint32_t i = 0; i < nb; ++i) {
-            const flinng_request &r = reqs[slot.reqs[i]];
-            hk[i] = r.k;
-            std::memcpy(hx + size_t(i) * ix->cfg.dim, r.data, size_t(ix->cfg.dim) * sizeof(float));
-        }
-        in_bytes = size_t(nb) * ix->cfg.dim * sizeof(float);
-        FL_CUDA(cudaMemcpyAsync(d + Lo.k, h + Lo.k, nb * sizeof(uint32_t), cudaMemcpyHostToDevice, slot.stream));
-        FL_CUDA(cudaMemcpyAsync(d + Lo.in_el, h + Lo.in_el, in_bytes, cudaMemcpyHostToDevice, slot.stream));
     } else {
-        uint64_t *ho = reinterpret_cast<uint64_t *>(h + Lo.in_off);
-        uint32_t *he = reinterpret_cast<uint32_t *>(h + Lo.in_el);
-        ho[0] = 0;
-        for (uint32_t i = 0; i < nb; ++i) {
-            const flinng_request &r = reqs[slot.reqs[i]];
-            hk[i] = r.k;
-            std::memcpy(he + ho[i], r.data, size_t(r.n) * sizeof(uint32_t));
-            ho[i + 1] = ho[i] + r.n;
+        size_t in_bytes;
+        if (srp) {
+            float *hx = reinterpret_cast<float *>(h + Lo.in_el);
+            for (uint32_t i = 0; i < nb; ++i) {
+                const flinng_request &r = reqs[slot.reqs[i]];
+                hk[i] = r.k;
+                std::memcpy(hx + size_t(i) * ix->cfg.dim, r.data, size_t(ix->cfg.dim) * sizeof(float));
+            }
+            in_bytes = size_t(nb) * ix->cfg.dim * sizeof(float);
+        } else {
+            uint32_t *he = reinterpret_cast<uint32_t *>(h + Lo.in_el);
+            for (uint32_t i = 0; i < nb; ++i) {
+                const flinng_request &r = reqs[slot.reqs[i]];
+                hk[i] = r.k;
+                std::memcpy(he + ho[i], r.data, size_t(r.n) * sizeof(uint32_t));
+                ho[i + 1] = ho[i] + r.n;
+            }
+            in_bytes = size_t(ho[nb]) * sizeof(uint32_t);
         }
-        in_bytes = size_t(ho[nb]) * sizeof(uint32_t);
-        FL_CUDA(cudaMemcpyAsync(d + Lo.k, h + Lo.k, nb * sizeof(uint32_t), cudaMemcpyHostToDevice, slot.stream));
-        FL_CUDA(cudaMemcpyAsync(d + Lo.in_off, h + Lo.in_off, (nb + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice,
-                                slot.stream));
+        FL_CUDA(cudaMemcpyAsync(dh, hh, ho_.bytes, cudaMemcpyHostToDevice, slot.stream));
         if (in_bytes)
             FL_CUDA(cudaMemcpyAsync(d + Lo.in_el, h + Lo.in_el, in_bytes, cudaMemcpyHostToDevice, slot.stream));
     }
@@ -210,7 +225,7 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
     ix->qnext = reinterpret_cast<uint32_t *>(d);
     ix->stats = reinterpret_cast<unsigned long long *>(d) + 2;
     int rc = FLINNG_OK;
-    const uint32_t *dk = reinterpret_cast<const uint32_t *>(d + Lo.k);
+    const uint32_t *dk = reinterpret_cast<const uint32_t *>(dh + ho_.k);
     uint32_t *dids = reinterpret_cast<uint32_t *>(d + Lo.ids);
     uint16_t *dsc = reinterpret_cast<uint16_t *>(d + Lo.sc);
     const bool big_srp = srp && uint64_t(ix->P) * ix->cfg.dim > (1ull << 18);
@@ -221,7 +236,7 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
         if (rc == FLINNG_OK) rc = query_launch(ix, qb, nb, dk, km, dids, dsc);
     } else {
         FusedQuery fq{nb, reinterpret_cast<const float *>(d + Lo.in_el), ix->cfg.dim,
-                      reinterpret_cast<const uint64_t *>(d + Lo.in_off), reinterpret_cast<const uint32_t *>(d + Lo.in_el)};
+                      reinterpret_cast<const uint64_t *>(dh + ho_.in_off), reinterpret_cast<const uint32_t *>(d + Lo.in_el)};
         uint32_t bucket = 0;
         while ((1u << bucket) < nb) ++bucket;
         const QueryTuning *tune = ix->tuning[bucket].valid ? &ix->tuning[bucket] : nullptr;
@@ -262,9 +277,17 @@ int flinng_server_create(const flinng_server_config *cfg, flinng_server **out)
             srv->device_gather = pageable != 0;
     }
     srv->slots.resize(cfg->n_slots);
+    {
+        const cudaError_t e = cudaEventCreate(&srv->ref);
+        if (e != cudaSuccess) {
+            flinng_server_destroy(srv);
+            return cuda_error(e, "server events");
+        }
+    }
     for (Slot &s : srv->slots) {
         cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreate(&s.start);
+        if (e == cudaSuccess) e = cudaEventCreate(&s.done);
         if (e != cudaSuccess) {
             flinng_server_destroy(srv);
             return cuda_error(e, "server streams");
@@ -279,11 +302,13 @@ int flinng_server_destroy(flinng_server *srv)
     if (!srv) return FLINNG_OK;
     for (Slot &s : srv->slots) {
         if (s.stream) cudaStreamSynchronize(s.stream);
+        if (s.start) cudaEventDestroy(s.start);
         if (s.done) cudaEventDestroy(s.done);
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.dscratch) cudaFree(s.dscratch);
         if (s.hstage) cudaFreeHost(s.hstage);
     }
+    if (srv->ref) cudaEventDestroy(srv->ref);
     delete srv;
     return FLINNG_OK;
 }
@@ -351,6 +376,7 @@ int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_
         S.pending.clear();
         S.inflight = 0;
     }
+    if (n) FL_CUDA(cudaEventRecord(srv->ref, srv->slots[0].stream));
     const double t0 = now_s();
     uint64_t next = 0, done = 0, batches = 0;
     size_t rr = 0;
@@ -363,12 +389,20 @@ int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_
         }
         bool progress = false;
         // harvest finished batches
-        for (Slot &s : srv->slots) {
+        for (size_t si = 0; si < srv->slots.size(); ++si) {
+            Slot &s = srv->slots[si];
             if (!s.busy) continue;
             const cudaError_t q = cudaEventQuery(s.done);
             if (q == cudaErrorNotReady) continue;
             if (q != cudaSuccess) return cuda_error(q, "replay: batch");
             const double t = now_s() - t0;
+            // device times of the batch (both events and the origin have completed)
+            float ms0 = -1.0f, ms1 = -1.0f;
+            if (cudaEventElapsedTime(&ms0, srv->ref, s.start) != cudaSuccess ||
+                cudaEventElapsedTime(&ms1, srv->ref, s.done) != cudaSuccess) {
+                ms0 = ms1 = -1.0f;
+                (void)cudaGetLastError();   // not sticky: clear it so later launch checks stay clean
+            }
             const char *h = static_cast<const char *>(s.hstage);
             for (size_t i = 0; i < s.reqs.size(); ++i) {
                 const uint64_t r = s.reqs[i];
@@ -377,6 +411,9 @@ int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_
                     std::memcpy(out_scores + r * km, h + Lo.sc + i * km * sizeof(uint16_t), km * sizeof(uint16_t));
                 res[r].t_done = t;
                 res[r].status = FLINNG_OK;
+                res[r].slot = uint32_t(si);
+                res[r].d_start = ms0 * 1e-3;
+                res[r].d_done = ms1 * 1e-3;
             }
             done += s.reqs.size();
             srv->idx[s.index].inflight--;

@@ -559,7 +559,7 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
     const double g2d = 2.0 * d * std::ldexp(1.0, -24) / (1.0 - 2.0 * d * std::ldexp(1.0, -24));
     const float g2 = std::nextafter(float(2.0 * g2d * g2d + std::ldexp(1.0, -40)), INFINITY);
     const size_t smem = size_t(kStages) * kStageBytes + 1024 + 256;
-    FL_CUDA(cudaFuncSetAttribute(k_srp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FL_TRY(ensure_dyn_smem((const void *)k_srp_tc, smem));
     for (uint64_t r0 = 0; r0 < n; r0 += chunk) {
         const uint64_t rows = (n - r0) < chunk ? (n - r0) : chunk;
         k_split_rows<<<warp_grid(rows), 256, 0, st>>>(x + r0 * ld, ld, rows, d, xs, xs + rows * d, xn);

@@ -53,7 +53,8 @@ class flinng_request(C.Structure):
 
 class flinng_request_result(C.Structure):
     _fields_ = [("t_admit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
-                ("status", C.c_uint32), ("version", C.c_uint32), ("batch", C.c_uint32), ("reserved", C.c_uint32)]
+                ("status", C.c_uint32), ("version", C.c_uint32), ("batch", C.c_uint32), ("slot", C.c_uint32),
+                ("d_start", C.c_double), ("d_done", C.c_double)]
 
 
 REQ_QUERY, REQ_INSERT = 0, 1
@@ -63,7 +64,8 @@ REQ_DTYPE = np.dtype([("arrival_s", "<f8"), ("kind", "<u4"), ("index", "<u4"), (
                       ("on_device", "<u4"), ("n", "<u8"), ("data", "<u8"), ("perm", "<u8")], align=True)
 assert REQ_DTYPE.itemsize == C.sizeof(flinng_request)
 RES_DTYPE = np.dtype([("t_admit", "<f8"), ("t_start", "<f8"), ("t_done", "<f8"), ("status", "<u4"),
-                      ("version", "<u4"), ("batch", "<u4"), ("reserved", "<u4")], align=True)
+                      ("version", "<u4"), ("batch", "<u4"), ("slot", "<u4"), ("d_start", "<f8"),
+                      ("d_done", "<f8")], align=True)
 assert RES_DTYPE.itemsize == C.sizeof(flinng_request_result)
 
 
@@ -520,14 +522,26 @@ class Server:
         'host copy' (inputs copied into pinned staging first)."""
         return "device gather" if self.lib.flinng_server_staging(self.h) == 1 else "host copy"
 
-    def replay(self, reqs):
+    def replay(self, reqs, out=None):
         """reqs: a ctypes array of flinng_request or a numpy array of
         REQ_DTYPE (kept alive by the caller, with every buffer it points to).
+        out: optional (ids, scores) host arrays of at least len(reqs) rows of
+        k_max (uint32, uint16, C-contiguous), reused across replays; by
+        default fresh arrays, written once here so that the replay does not
+        pay the first touch of their pages.
         Returns (ids, scores, results); results is a ctypes array for ctypes
         input, a numpy array of RES_DTYPE for numpy input."""
         n = len(reqs)
-        ids = np.zeros((max(n, 1), self.k_max), np.uint32)
-        sc = np.zeros((max(n, 1), self.k_max), np.uint16)
+        if out is None:
+            ids = np.empty((max(n, 1), self.k_max), np.uint32)
+            sc = np.empty((max(n, 1), self.k_max), np.uint16)
+            ids.fill(0)
+            sc.fill(0)
+        else:
+            ids, sc = out
+            assert (ids.dtype == np.uint32 and sc.dtype == np.uint16 and ids.flags.c_contiguous and
+                    sc.flags.c_contiguous and ids.shape[0] >= n and sc.shape[0] >= n and
+                    ids.shape[1] == self.k_max and sc.shape[1] == self.k_max)
         if isinstance(reqs, np.ndarray):
             assert reqs.dtype == REQ_DTYPE and reqs.flags.c_contiguous
             res = np.zeros(max(n, 1), RES_DTYPE)

@@ -105,3 +105,49 @@ def test_recorded_traffic_needs_the_same_kernel_source(monkeypatch):
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.recorded_traffic("C2") is None
     assert bench.recorded_traffic("C9") is None
+
+
+def test_fixed_size_trace_and_k_choice():
+    rng = np.random.default_rng(3)
+    qoff = np.array([0, 3, 3, 10, 12], np.uint64)
+    src = {"id": 0, "kind": "sets", "share": 1.0, "nq": 4, "sizes": np.diff(qoff), "off": qoff[:-1],
+           "base": np.uint64(1 << 20)}
+    req = bench.make_trace(F, rng, rate=1e6, T=0.0, sources=[src], k_choices=(100,), n=5000)
+    assert len(req) == 5000 and np.all(req["k"] == 100)
+    assert req["arrival_s"].max() <= 5000 / 1e6 and np.all(np.diff(req["arrival_s"]) >= 0)
+
+
+def test_serving_step_and_latency_breakdown():
+    n = 400
+    req = np.zeros(n, F.REQ_DTYPE)
+    req["arrival_s"] = np.linspace(0.0, 0.01, n)
+    res = np.zeros(n, F.RES_DTYPE)
+    res["t_start"] = req["arrival_s"] + 1e-4         # 0.1 ms waiting for a slot
+    res["d_start"] = res["t_start"] + 2e-5           # 0.02 ms to the first device event
+    res["d_done"] = res["d_start"] + 3e-4            # 0.3 ms on the device
+    res["t_done"] = res["d_done"] + 5e-5             # 0.05 ms to the caller's buffer
+    res["batch"] = np.arange(n) // 50
+    st = bench.serving_step_stats(req, res, F)
+    assert st["queries"] == n and st["batches"] == 8
+    assert st["device_s"] == pytest.approx(res["d_done"].max() - res["d_start"].min())
+    assert st["host_s"] == pytest.approx(0.01 + 1e-4 + 2e-5 + 3e-4 + 5e-5)
+    b = bench.latency_breakdown(req, res, F)
+    for part, ms in (("wait", 0.1), ("launch", 0.02), ("device", 0.3), ("harvest", 0.05)):
+        assert b[part]["p50"] == pytest.approx(ms, rel=1e-6) and b[part]["p99"] == pytest.approx(ms, rel=1e-6)
+
+
+def test_recall_target_workload_and_shared_config():
+    c = {"metric": "jaccard", "seed": 11, "N": 50, "nq": 3, "k": 100, "R": 2, "B": 10, "L": 32, "K": 2, "W": 17,
+         "desc": "sets N=50 R2 B10 L32 K2 W17 nq=3 k=100"}
+    bench.TARGETS["T9"] = dict(R=3, B=16, L=64, K=1, W=17)
+    try:
+        ct = bench.target_workload(c, "T9")
+        assert (ct["R"], ct["B"], ct["L"], ct["K"], ct["W"]) == (3, 16, 64, 1, 17)
+        assert ct["perm"].shape == (3, 50) and all(sorted(r) == list(range(50)) for r in ct["perm"])
+        assert len(ct["params"]["bucket_a"]) == 64 * 1
+        assert "R3 B16 L64 K1 W17" in ct["desc"] and ct["configured"]["L"] == 32
+        # both arms print the same config object
+        assert bench.headline_config("T9", ct, 1) == bench.headline_config("T9", dict(ct), 1)
+        assert bench.headline_config("T9", ct, 2)["global_batch"] == 2 * bench.SERVE_QUERIES
+    finally:
+        del bench.TARGETS["T9"]

@@ -4,7 +4,8 @@ A Poisson trace of queries (k in {1, 10, 100}, uneven set sizes) against a
 MinHash index and a cosine index, interleaved with insert batches. Every
 served result must equal flinng_query run alone on a replica of its index at
 the same version (inserts applied before the query ran), batches must have
-overlapped in time, and admission must respect the HBM budget.
+overlapped in time (host clock, and CUDA events on the device), and admission
+must respect the HBM budget.
 """
 import ctypes as C
 
@@ -142,5 +143,18 @@ def test_serving_matches_queries_alone(F):
         spans[b] = (min(s0, res[i].t_start), max(s1, res[i].t_done))
     sp = sorted(spans.values())
     assert any(sp[j + 1][0] < sp[j][1] for j in range(len(sp) - 1)), "no two batches were in flight together"
+    # the same on the device clock: CUDA events on each batch's stream slot
+    # (first copy in .. results out) show batches of different slots running
+    # at once on the GPU
+    dev = {}
+    for i in qs:
+        b = res[i].batch
+        assert 0.0 <= res[i].d_start <= res[i].d_done, (res[i].d_start, res[i].d_done)
+        assert res[i].slot < 4
+        dev[b] = (res[i].d_start, res[i].d_done, res[i].slot)
+    ds = sorted(dev.values())
+    overlap = [(a, b) for a, b in zip(ds, ds[1:]) if b[0] < a[1] and b[2] != a[2]]
+    assert overlap, "no two batches overlapped on the device"
+    assert len({v[2] for v in dev.values()}) >= 2
     assert len({res[i].version for i, e in enumerate(reqs_py) if e[0] == "a"}) >= 2
     srv.close()
