@@ -361,12 +361,14 @@ __device__ void gather_counts(const QArgs &a, const QSmem &s, const uint32_t *qb
         uint32_t beg = 0, len = 0;
         if (l < a.L) {
             const uint64_t slot = (uint64_t(l) << a.W) | qb[l];
+            // the three loads go out together (one round trip, not two)
             const uint32_t h = a.hidx[slot];
+            const uint32_t o0 = a.off[slot], o1 = a.off[slot + 1];
             if (h != kEmpty32) {
                 s.g_hl[atomicAdd(&s.u[5], 1u)] = h;
             } else {
-                beg = a.off[slot];
-                len = a.off[slot + 1] - beg;
+                beg = o0;
+                len = o1 - o0;
             }
         }
         if (tid == 0) s.c_pre[NT] = ~0u;   // ends every forward search of c_pre
@@ -564,12 +566,25 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
         // Levels are taken in groups: level t and the levels below it while the
         // group holds at most a.gcells cells (about 4,096 members). A group's
         // cells are contiguous in lvl_cells (levels descending).
+        // After the placement above, lvl_cur[v] is the number of cells at levels
+        // >= v (non-increasing in v), so a group's extent is a binary search,
+        // not a walk over the (mostly empty) levels.
         int t = int(a.L);
         while (t >= int(a.t_min)) {
-            uint32_t nc = s.lvl_n[t];
+            const uint32_t first = s.lvl_cur[t] - s.lvl_n[t];   // cells at levels above t
+            const uint32_t lim = first + a.gcells;
             int t_end = t;
-            while (t_end > int(a.t_min) && nc + s.lvl_n[t_end - 1] <= a.gcells) nc += s.lvl_n[--t_end];
-            const uint32_t first = s.lvl_cur[t] - s.lvl_n[t];
+            if (s.lvl_cur[t] <= lim) {
+                // the lowest t_end in [t_min, t] whose levels [t_end, t] hold <= gcells cells
+                int lo = int(a.t_min), hi = t;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s.lvl_cur[mid] <= lim) hi = mid;
+                    else lo = mid + 1;
+                }
+                t_end = lo;
+            }
+            const uint32_t nc = s.lvl_cur[t_end] - first;
             for (uint32_t c0 = 0; c0 < nc; c0 += NT) {
                 const uint32_t ci = c0 + tid;
                 uint32_t ms = 0, sz = 0, b = 0, lev = 0;

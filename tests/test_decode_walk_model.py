@@ -98,3 +98,56 @@ def test_kernel_walk_equals_alg3(seed):
         ids, sc, n = O.alg3(cnt, moff, mem, N, R, B, k=kq, t_min=t_min)
         w_ids, w_sc = kernel_walk(cnt, gid, B, L, kq, t_min, gcells, cap_fill, rng)
         assert w_ids == ids[:n].tolist() and w_sc == sc[:n].tolist(), (kq, gcells, cap_fill)
+
+
+def group_extent_linear(lvl_n, t, t_min, gcells):
+    """The group rule as stated: level t, then the levels below it while the
+    group holds at most gcells cells."""
+    nc, t_end = lvl_n[t], t
+    while t_end > t_min and nc + lvl_n[t_end - 1] <= gcells:
+        t_end -= 1
+        nc += lvl_n[t_end]
+    return t_end, nc
+
+
+def group_extent_bsearch(lvl_n, t, t_min, gcells):
+    """The kernels' form: ge[v] = cells at levels >= v (the level placement's
+    end cursors), first = ge[t] - lvl_n[t], then a binary search for the lowest
+    t_end with ge[t_end] <= first + gcells (level t always belongs)."""
+    L = len(lvl_n) - 1
+    ge = [0] * (L + 2)
+    for v in range(L, -1, -1):
+        ge[v] = ge[v + 1] + lvl_n[v]
+    first = ge[t] - lvl_n[t]
+    lim = first + gcells
+    t_end = t
+    if ge[t] <= lim:
+        lo, hi = t_min, t
+        while lo < hi:
+            mid = (lo + hi) >> 1
+            if ge[mid] <= lim:
+                hi = mid
+            else:
+                lo = mid + 1
+        t_end = lo
+    return t_end, ge[t_end] - first
+
+
+@pytest.mark.parametrize("seed", range(200))
+def test_group_extent_binary_search_equals_walk(seed):
+    rng = np.random.default_rng(1000 + seed)
+    L = int(rng.integers(1, 600))
+    t_min = int(rng.integers(1, min(L, 4) + 1))
+    # mostly empty levels with a few crowded ones, as at high table counts
+    lvl_n = np.zeros(L + 1, np.int64)
+    busy = rng.choice(np.arange(t_min, L + 1), size=int(rng.integers(0, min(L - t_min + 1, 40) + 1)),
+                      replace=False)
+    lvl_n[busy] = rng.integers(1, 400, size=len(busy))
+    lvl_n = lvl_n.tolist()
+    for gcells in (1, 7, int(rng.integers(1, 500)), 10 ** 6):
+        t = L
+        while t >= t_min:
+            a = group_extent_linear(lvl_n, t, t_min, gcells)
+            b = group_extent_bsearch(lvl_n, t, t_min, gcells)
+            assert a == b, (t, gcells)
+            t = a[0] - 1
