@@ -235,11 +235,13 @@ k_doph(const uint64_t *__restrict__ off, const uint32_t *__restrict__ elems,
         }
         __syncwarp();
         if (end > beg) {
+            const bool pow2 = (nb & (nb - 1u)) == 0u;     // z mod nb is a mask then
             for (uint32_t k = lane; k < nb; k += 32) {
                 if ((occ[k >> 5] >> (k & 31)) & 1u) continue;
                 bool found = false;
                 for (uint32_t att = 1; att <= kDophMaxAttempts; ++att) {
-                    const uint32_t j = uint32_t(splitmix64(seed ^ ((uint64_t(k) << 32) | att)) % nb);
+                    const uint64_t z = splitmix64(seed ^ ((uint64_t(k) << 32) | att));
+                    const uint32_t j = pow2 ? uint32_t(z) & (nb - 1u) : uint32_t(z % nb);
                     if ((occ[j >> 5] >> (j & 31)) & 1u) {
                         val[k] = val[j];
                         found = true;

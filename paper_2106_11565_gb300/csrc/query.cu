@@ -158,10 +158,20 @@ static int fused_prepare(flinng_index *ix, const FusedQuery &fq, const uint32_t 
         hash_bytes += size_t(h.nb + (h.nb + 31) / 32) * 4;
     }
     hash_bytes = (hash_bytes + 15) & ~size_t(15);
+    // The hash region (query buckets, hash scratch, the query slot) is live
+    // only before the decode keeps candidates, so it shares the candidate
+    // buffer with the gather's heavy-table list (the buffer's last NT words)
+    // when both fit; otherwise it follows the query state.
     size_t qbytes;
-    pick_buffer(a, NT, tune, hash_bytes, &qbytes, int(ix->cw), 1);
-    h.hash_off = qbytes;
-    P->smem = qbytes + hash_bytes;
+    pick_buffer(a, NT, tune, 0, &qbytes, int(ix->cw), 1);
+    if (hash_bytes + size_t(NT) * 4 <= size_t(a.cap) * 8) {
+        h.hash_off = 0;
+        P->smem = qbytes;
+    } else {
+        pick_buffer(a, NT, tune, hash_bytes, &qbytes, int(ix->cw), 1);
+        h.hash_off = qbytes;
+        P->smem = qbytes + hash_bytes;
+    }
     if (P->smem > 227 * 1024)
         return set_error(FLINNG_ERR_INVALID_ARG, "fused query: %zu bytes of shared memory needed (> 227 KB)", P->smem);
     P->fn = ix->cw == 1 ? fused_kernel_c1(NT, ix->rw, srp) : fused_kernel_c2(NT, ix->rw, srp);
@@ -270,7 +280,7 @@ int counts_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
 {
     if (nq == 0) return FLINNG_OK;
     QArgs a = make_args(ix, qbuckets, nq);
-    a.cap = 2;
+    a.cap = kQTmax / 2;      // the heavy-table list takes the buffer's last kQTmax words
     a.kp = 2;
     a.out_counts = out_counts;
     const size_t smem = qsmem_bytes(a.cap, a.kp, a.BR, a.B, kQTmax, a.L, int(ix->cw));

@@ -82,7 +82,8 @@ struct QSmem {
     uint32_t *c_pre;     // NT + 4: exclusive prefix of member (list) lengths; c_pre[NT] = ~0
     uint2 *c_rec;        // NT: per cell of a chunk {record base, cell | level << 16}
     uint32_t *c_start;   // NT: per table of a chunk, list base (gather; shares c_rec's space)
-    uint32_t *g_hl;      // NT: bitmap indices of the heavy tables of a chunk of tables
+    uint32_t *g_hl;      // NT: bitmap indices of the heavy tables of a chunk of tables (the last
+                         // NT words of buf: the gather runs before any candidate is kept)
     uint32_t *wsum;      // NT / 32: block-scan scratch
     uint32_t *cntw;      // count words: 4 byte counts (CW = 1) or 2 16-bit counts (CW = 2) each
     uint16_t *lvl_cells; // B
@@ -96,7 +97,7 @@ __host__ __device__ inline size_t qsmem_bytes(uint32_t cap, uint32_t kp, uint32_
                                               int cw)
 {
     size_t b = size_t(cap) * 8 + size_t(kp) * 8 + 8 * 4 + 2 * size_t(q_nlev(L)) * 4 + 256 * 4 +
-               (NT + 4) * 4 + 2 * NT * 4 + NT * 4 + (NT / 32) * 4;
+               (NT + 4) * 4 + 2 * NT * 4 + (NT / 32) * 4;
     b = (b + 15) & ~size_t(15);
     b += size_t(q_count_words(BR, cw)) * 4;
     b += size_t(B) * 2;
@@ -117,8 +118,8 @@ __device__ inline QSmem carve_q(unsigned char *sm, uint32_t cap, uint32_t kp, ui
     s.c_pre = s.rhist + 256;
     s.c_rec = reinterpret_cast<uint2 *>(s.c_pre + NT + 4);   // 8-byte aligned: offsets are even
     s.c_start = reinterpret_cast<uint32_t *>(s.c_rec);
-    s.g_hl = reinterpret_cast<uint32_t *>(s.c_rec + NT);
-    s.wsum = s.g_hl + NT;
+    s.g_hl = reinterpret_cast<uint32_t *>(s.buf + cap) - NT;   // needs 2 cap >= NT
+    s.wsum = reinterpret_cast<uint32_t *>(s.c_rec + NT);
     size_t o = (size_t)((unsigned char *)(s.wsum + NT / 32) - sm);
     o = (o + 15) & ~size_t(15);
     s.cntw = (uint32_t *)(sm + o);
@@ -612,9 +613,9 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                 const uint32_t per = ((M + NT / 32 - 1) / (NT / 32) + 31) & ~31u;
                 uint32_t jb = min(uint32_t(tid >> 5) * per, M);   // this warp's cursor (warp-uniform)
                 const uint32_t je = min(jb + per, M);
-                uint32_t hint[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) hint[u] = jb + uint32_t(u) * 32 + lane < je ? find_seg(s.c_pre, ncc, jb + uint32_t(u) * 32 + lane) : 0u;
+                // the cell holding member jb (warp-uniform; the largest such index
+                // is never an empty cell)
+                uint32_t cur = jb < je ? find_seg(s.c_pre, ncc, jb) : 0u;
                 // Members are decoded without per-round reservations: a warp about
                 // to append reads the buffer fill first and appends only while it
                 // is at or below hwm. Above it the warp pauses; once every warp has
@@ -626,6 +627,21 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                 for (;;) {
                     const uint32_t smin = max(a.t_min, bscore);   // lower scores cannot enter
                     while (jb < je) {
+                        // lanes to cells: one warp-uniform pass over the cell
+                        // boundaries inside this step (a cell or two for 32 members);
+                        // c_pre is M at the chunk's end and ~0 at NT, so the pass
+                        // stops at the step's last member
+                        const uint32_t last_j = min(jb + 32u * U, je) - 1u;
+                        uint32_t my[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) my[u] = cur;
+                        uint32_t k = cur + 1, bnd = s.c_pre[k];
+                        while (bnd <= last_j) {
+#pragma unroll
+                            for (int u = 0; u < U; ++u)
+                                if (jb + uint32_t(u) * 32 + lane >= bnd) my[u] = k;
+                            bnd = s.c_pre[++k];
+                        }
                         uint32_t w[U][RW];
                         uint32_t cell[U];
                         bool in[U];
@@ -635,17 +651,7 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                             in[u] = j < je;
                             cell[u] = 0;
                             if (in[u]) {
-                                // c_pre is M past the chunk's last cell and ~0 at NT
-                                uint32_t cs = hint[u];
-                                for (int step = 0; s.c_pre[cs + 1] <= j; ++step) {
-                                    if (step == 4) {
-                                        cs = find_seg(s.c_pre, ncc, j, cs + 1);
-                                        break;
-                                    }
-                                    ++cs;
-                                }
-                                hint[u] = cs;
-                                const uint2 cr = s.c_rec[cs];
+                                const uint2 cr = s.c_rec[my[u]];
                                 cell[u] = cr.y;
                                 load_record<RW>(a.mrec, cr.x + j, w[u]);
                             }
@@ -695,6 +701,7 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
                             }
                         }
                         jb += 32 * U;
+                        cur = k - 1;   // the cell holding member last_j
                     }
                     __syncthreads();
                     const uint32_t nb0 = s.u[0];   // same value in every thread (read after the barrier)
@@ -809,7 +816,8 @@ struct HArgs {
     unsigned long long *stats;
     uint32_t *qnext;    // next query to hand out (zeroed before each launch)
     uint32_t K;
-    size_t hash_off;    // byte offset of the hash region in shared memory
+    size_t hash_off;    // byte offset of the hash region in shared memory (0: inside the
+                        // candidate buffer, which is free until the decode)
 };
 
 __device__ __forceinline__ uint64_t splitmix64_q(uint64_t z)
@@ -839,11 +847,13 @@ __device__ void cta_doph(const QArgs &a, const HArgs &h, uint32_t q, uint32_t *q
     }
     __syncthreads();
     if (end > beg) {
+        const bool pow2 = (nb & (nb - 1u)) == 0u;     // z mod nb is a mask then
         for (uint32_t k = tid; k < nb; k += NT) {
             if ((occ[k >> 5] >> (k & 31)) & 1u) continue;
             bool found = false;
             for (uint32_t att = 1; att <= kDophMaxAttempts; ++att) {
-                const uint32_t j = uint32_t(splitmix64_q(h.seed ^ ((uint64_t(k) << 32) | att)) % nb);
+                const uint64_t z = splitmix64_q(h.seed ^ ((uint64_t(k) << 32) | att));
+                const uint32_t j = pow2 ? uint32_t(z) & (nb - 1u) : uint32_t(z % nb);
                 if ((occ[j >> 5] >> (j & 31)) & 1u) {
                     val[k] = val[j];
                     found = true;

@@ -386,7 +386,7 @@ def test_graph_replay_and_tuning_keep_results(F):
         ids, sc = ix.query(sl(*r), 30)
         assert np.array_equal(ids, rid) and np.array_equal(sc, rsc)
     ch = ix.tune(sl(0, 300), 30)
-    assert ch["threads"] in (128, 256)
+    assert ch["threads"] in (128, 256, 512)        # any shape the tuner knows
     for r, (rid, rsc) in list(ref.items())[::-1]:
         ids, sc = ix.query(sl(*r), 30)
         assert np.array_equal(ids, rid) and np.array_equal(sc, rsc)

@@ -12,6 +12,10 @@ their plain definitions (no GPU).
   one (four steps, then a binary search), ended by the prefix sums past the
   last list and a sentinel at NT. The model must visit every entry exactly
   once, in its own list, with empty lists anywhere.
+* The decode's member walk: a warp-uniform cursor holds the cell of the
+  step's first member, and one pass over the cell boundaries inside the step
+  maps every lane to its cell. The model must visit every member exactly
+  once, in its own cell, with empty cells anywhere.
 * The radix select that cuts a buffer of more than 256 candidates to the k
   best: the (prefix, mask) it returns must keep exactly the k smallest keys,
   for 8- and 16-bit score fields and long runs of equal leading digits.
@@ -149,6 +153,70 @@ def test_slice_walk_visits_every_entry_once_in_its_list(seed):
     assert sorted(e for e, _ in seen) == list(range(total))
     for e, t in seen:
         assert pre[t] <= e < pre[t] + lens[t] and lens[t] > 0
+
+
+def cursor_walk(lens, NT, U):
+    """Members visited by the decode's walk: each warp takes a contiguous slice;
+    a warp-uniform cursor (the cell holding the step's first member) and one
+    pass over the cell boundaries inside each step map lanes to cells. Returns
+    (member, cell) pairs, and the number of boundary reads per step."""
+    n = len(lens)
+    assert n <= NT
+    pre = np.zeros(NT + 1, np.int64)
+    total = int(sum(lens))
+    run = 0
+    for t in range(NT):
+        pre[t] = run
+        run += lens[t] if t < n else 0
+    pre[NT] = M32                               # the sentinel
+    seen, reads = [], []
+    nwarps = NT // 32
+    per = ((total + nwarps - 1) // nwarps + 31) & ~31
+    for w in range(nwarps):
+        jb = min(w * per, total)
+        je = min(jb + per, total)
+        cur = find_seg(pre, n, jb) if jb < je else 0
+        while jb < je:
+            last_j = min(jb + 32 * U, je) - 1
+            my = [[cur] * 32 for _ in range(U)]
+            k = cur + 1
+            bnd = pre[k]
+            nread = 1
+            while bnd <= last_j:
+                for u in range(U):
+                    for lane in range(32):
+                        if jb + u * 32 + lane >= bnd:
+                            my[u][lane] = k
+                k += 1
+                bnd = pre[k]
+                nread += 1
+            reads.append(nread)
+            for u in range(U):
+                for lane in range(32):
+                    j = jb + u * 32 + lane
+                    if j < je:
+                        seen.append((j, my[u][lane]))
+            jb += 32 * U
+            cur = k - 1
+    return seen, pre, reads
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_cursor_walk_visits_every_member_once_in_its_cell(seed):
+    rng = np.random.default_rng(500 + seed)
+    NT = int(rng.choice([128, 256, 512]))
+    U = int(rng.choice([1, 4]))
+    n = int(rng.integers(1, NT + 1))
+    # empty cells anywhere (skipped cells have no members), runs of tiny ones
+    lens = rng.choice([0, 0, 0, 1, 2, 24, 25, 100, 500], size=n).tolist()
+    seen, pre, reads = cursor_walk(lens, NT, U)
+    total = int(sum(lens))
+    assert sorted(j for j, _ in seen) == list(range(total))
+    for j, c in seen:
+        assert pre[c] <= j < pre[c] + lens[c] and lens[c] > 0
+    # the pass reads one boundary per cell it crosses, plus one
+    if reads:
+        assert max(reads) <= 32 * U + NT
 
 
 # ---------------------------------------------------------------- radix select
