@@ -448,15 +448,20 @@ int flinng_server_add_index(flinng_server *srv, flinng_index *idx, uint32_t *ind
 /* Device bytes held by the registered indices and the slots. */
 uint64_t flinng_server_device_bytes(const flinng_server *srv);
 
-/* How the server stages query inputs: 1 = a kernel gathers them straight
- * from the requests' host buffers (the device can read pageable host
- * memory), 0 = the host copies them into pinned staging first. Negative:
+/* How the server stages query inputs and results: 1 = a kernel gathers the
+ * inputs straight from the requests' host buffers and the query kernel
+ * writes each result row straight into the caller's out_ids / out_scores
+ * (the device can read and write pageable host memory), 0 = the host copies
+ * inputs into pinned staging first and results back out of it. Negative:
  * an error code (NULL server). */
 int flinng_server_staging(const flinng_server *srv);
 
-/* Serve n requests, each admitted when the clock reaches its arrival time;
- * returns when all are done. out_ids / out_scores: n x k_max (HOST), rows of
- * queries written (padding as flinng_query), rows of inserts untouched.
+/* Serve n requests (n < 2^32), each admitted when the clock reaches its
+ * arrival time; returns when all are done. out_ids / out_scores: n x k_max
+ * (HOST), rows of queries written (padding as flinng_query), rows of inserts
+ * untouched. With staging 1 (flinng_server_staging) the GPU writes the rows
+ * itself: the buffers must stay valid for the whole call, and pages touched
+ * beforehand avoid first-touch faults during the replay.
  * res: per-request times, status, index version and batch.
  * Errors: INVALID_ARG (bad request, checked before anything runs), CUDA. */
 int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_t n,

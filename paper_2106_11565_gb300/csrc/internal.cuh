@@ -203,6 +203,7 @@ struct FusedQuery {
     uint64_t ldx;
     const uint64_t *off;     // Jaccard: device CSR
     const uint32_t *elems;
+    const uint32_t *out_row = nullptr;   // per query: its output row, or null (row = query index)
 };
 int query_fused_launch(flinng_index *ix, const FusedQuery &fq, const uint32_t *k, uint32_t k_max,
                        uint32_t *out_ids, uint16_t *out_scores, const QueryTuning *tune);

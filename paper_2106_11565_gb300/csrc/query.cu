@@ -25,6 +25,7 @@ QArgs make_args(flinng_index *ix, const uint32_t *qb, uint32_t nq)
     a.hidx = ix->hidx;
     a.hbm = ix->hbm;
     a.BRw = ix->BRw;
+    a.heavy_min = ix->heavy_min;
     a.L = ix->cfg.L;
     a.W = ix->cfg.range_bits;
     a.R = ix->cfg.R;
@@ -131,6 +132,7 @@ static int fused_prepare(flinng_index *ix, const FusedQuery &fq, const uint32_t 
     a.k_max = k_max;
     a.out_ids = out_ids;
     a.out_scores = out_scores;
+    a.out_row = fq.out_row;
     h = HArgs{};
     const bool srp = ix->cfg.metric == FLINNG_COSINE_SRP;
     h.K = ix->cfg.K;

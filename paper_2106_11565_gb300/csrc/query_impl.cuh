@@ -63,12 +63,14 @@ struct QArgs {
     const uint32_t *hidx;     // per slot: heavy bitmap index or kEmpty32
     const uint32_t *hbm;      // heavy slots' cell bitmaps, BRw words each
     uint32_t L, W, R, B, BR, BRw, t_min;
+    uint32_t heavy_min; // a slot is heavy (has a cell bitmap) iff its list holds >= heavy_min cells
     uint32_t gcells;   // cells per level group of the decode (at least 1)
     uint32_t avg_cell; // members per repetition-0 cell, rounded up (host side, sizes gcells)
     uint32_t cap;      // candidate buffer entries (power of two)
     uint32_t kp;       // final sort width: power of two >= k_max
     uint32_t *out_ids;
     uint16_t *out_scores;
+    const uint32_t *out_row;  // per query: its row of the outputs, or null (row = query index)
     uint16_t *out_counts;
 };
 
@@ -362,11 +364,12 @@ __device__ void gather_counts(const QArgs &a, const QSmem &s, const uint32_t *qb
         uint32_t beg = 0, len = 0;
         if (l < a.L) {
             const uint64_t slot = (uint64_t(l) << a.W) | qb[l];
-            // the three loads go out together (one round trip, not two)
-            const uint32_t h = a.hidx[slot];
+            // the list's length decides whether the slot is heavy, so the
+            // bitmap index (another random DRAM access) is read for heavy
+            // slots only
             const uint32_t o0 = a.off[slot], o1 = a.off[slot + 1];
-            if (h != kEmpty32) {
-                s.g_hl[atomicAdd(&s.u[5], 1u)] = h;
+            if (o1 - o0 >= a.heavy_min) {
+                s.g_hl[atomicAdd(&s.u[5], 1u)] = a.hidx[slot];
             } else {
                 beg = o0;
                 len = o1 - o0;
@@ -761,12 +764,13 @@ __device__ void decode_topk(const QArgs &a, const QSmem &s, uint32_t q, uint32_t
             }
         }
     }
+    const size_t row = a.out_row ? size_t(a.out_row[q]) : size_t(q);
     for (uint32_t i = tid; i < a.k_max; i += NT) {
         const uint64_t key = (i < nk) ? s.keep[i] : kKeyNone;
         const bool ok = key != kKeyNone;
-        a.out_ids[size_t(q) * a.k_max + i] = ok ? uint32_t(key & 0xFFFFFFFFu) : 0xFFFFFFFFu;
+        a.out_ids[row * a.k_max + i] = ok ? uint32_t(key & 0xFFFFFFFFu) : 0xFFFFFFFFu;
         if (a.out_scores)
-            a.out_scores[size_t(q) * a.k_max + i] = ok ? uint16_t(kScoreMax - uint32_t(key >> 48)) : uint16_t(0);
+            a.out_scores[row * a.k_max + i] = ok ? uint16_t(kScoreMax - uint32_t(key >> 48)) : uint16_t(0);
     }
     __syncthreads();
 }

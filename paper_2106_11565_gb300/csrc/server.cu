@@ -17,8 +17,9 @@
 // Staging: where the GPU can read any host memory (pageable memory access,
 // e.g. over NVLink-C2C on Grace systems), a batch's inputs are gathered by a
 // kernel straight from the requests' own buffers, and the host only writes a
-// small descriptor per request. Elsewhere the host copies the inputs into
-// pinned staging first.
+// small descriptor per request; the query kernel then writes each result row
+// straight into the caller's output buffers too. Elsewhere the host copies
+// the inputs into pinned staging first and the results back out of it.
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -36,6 +37,7 @@ struct Slot {
     cudaEvent_t start = nullptr;   // recorded before the batch's first copy (timing)
     cudaEvent_t done = nullptr;    // recorded after its results reach the host staging (timing)
     bool busy = false;
+    bool direct = false;           // the batch's results go straight to the caller's buffers
     uint32_t index = 0;
     std::vector<uint64_t> reqs;
     // device scratch
@@ -64,7 +66,7 @@ struct Layout {
 // then nb + 1 input offsets, then nb values of k; `bytes` is what one copy
 // moves to the device.
 struct HdrOff {
-    size_t desc, in_off, k, bytes;
+    size_t desc, in_off, k, row, bytes;
 };
 
 // One request's input for the device gather: 4-byte words from a host
@@ -115,6 +117,7 @@ HdrOff hdr_for(uint64_t nb)
     h.desc = (size_t)c.take<GatherDesc>(nb);
     h.in_off = (size_t)c.take<uint64_t>(nb + 1);
     h.k = (size_t)c.take<uint32_t>(nb);
+    h.row = (size_t)c.take<uint32_t>(nb);
     h.bytes = c.used;
     return h;
 }
@@ -158,7 +161,11 @@ int size_slots(flinng_server *srv, size_t dbytes, size_t hbytes)
 }
 
 // Launch the queries in slot.reqs against index si on the slot's stream.
-int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
+// Where the device reads host memory directly, the query kernel writes each
+// result row straight into the caller's out_ids / out_scores (row = request
+// index); otherwise results come back through the slot's pinned staging.
+int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs, uint32_t *out_ids,
+                 uint16_t *out_scores)
 {
     TraceRange trace_("server batch");
     ServerIndex &S = srv->idx[slot.index];
@@ -173,7 +180,10 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
     char *hh = h + Lo.hdr;
     char *dh = d + Lo.hdr;
     uint32_t *hk = reinterpret_cast<uint32_t *>(hh + ho_.k);
+    uint32_t *hr = reinterpret_cast<uint32_t *>(hh + ho_.row);
     uint64_t *ho = reinterpret_cast<uint64_t *>(hh + ho_.in_off);
+    const bool big_srp = srp && uint64_t(ix->P) * ix->cfg.dim > (1ull << 18);
+    slot.direct = srv->device_gather && !big_srp;
     FL_CUDA(cudaEventRecord(slot.start, slot.stream));
     ho[0] = 0;
     if (srv->device_gather) {
@@ -182,6 +192,7 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
         for (uint32_t i = 0; i < nb; ++i) {
             const flinng_request &r = reqs[slot.reqs[i]];
             hk[i] = r.k;
+            hr[i] = uint32_t(slot.reqs[i]);
             const uint64_t n = srp ? uint64_t(ix->cfg.dim) : r.n;
             hd[i] = GatherDesc{reinterpret_cast<uint64_t>(r.data), ho[i], r.data ? n : 0};
             ho[i + 1] = ho[i] + n;
@@ -228,7 +239,6 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
     const uint32_t *dk = reinterpret_cast<const uint32_t *>(dh + ho_.k);
     uint32_t *dids = reinterpret_cast<uint32_t *>(d + Lo.ids);
     uint16_t *dsc = reinterpret_cast<uint16_t *>(d + Lo.sc);
-    const bool big_srp = srp && uint64_t(ix->P) * ix->cfg.dim > (1ull << 18);
     if (big_srp) {
         uint32_t *qb = reinterpret_cast<uint32_t *>(d + Lo.qb);
         rc = srp_hash(ix, reinterpret_cast<const float *>(d + Lo.in_el), ix->cfg.dim, nb, qb, nullptr, d + Lo.srp,
@@ -237,6 +247,11 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
     } else {
         FusedQuery fq{nb, reinterpret_cast<const float *>(d + Lo.in_el), ix->cfg.dim,
                       reinterpret_cast<const uint64_t *>(dh + ho_.in_off), reinterpret_cast<const uint32_t *>(d + Lo.in_el)};
+        if (slot.direct) {
+            fq.out_row = reinterpret_cast<const uint32_t *>(dh + ho_.row);
+            dids = out_ids;
+            dsc = out_scores;
+        }
         uint32_t bucket = 0;
         while ((1u << bucket) < nb) ++bucket;
         const QueryTuning *tune = ix->tuning[bucket].valid ? &ix->tuning[bucket] : nullptr;
@@ -246,10 +261,12 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs)
     ix->qnext = qn0;
     ix->stats = st0;
     FL_TRY(rc);
-    FL_CUDA(cudaMemcpyAsync(h + Lo.ids, d + Lo.ids, size_t(nb) * km * sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                            slot.stream));
-    FL_CUDA(cudaMemcpyAsync(h + Lo.sc, d + Lo.sc, size_t(nb) * km * sizeof(uint16_t), cudaMemcpyDeviceToHost,
-                            slot.stream));
+    if (!slot.direct) {
+        FL_CUDA(cudaMemcpyAsync(h + Lo.ids, d + Lo.ids, size_t(nb) * km * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                slot.stream));
+        FL_CUDA(cudaMemcpyAsync(h + Lo.sc, d + Lo.sc, size_t(nb) * km * sizeof(uint16_t), cudaMemcpyDeviceToHost,
+                                slot.stream));
+    }
     FL_CUDA(cudaEventRecord(slot.done, slot.stream));
     return FLINNG_OK;
 }
@@ -352,6 +369,7 @@ int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_
 {
     TraceRange trace_("flinng_server_replay");
     if (!srv || (n && (!reqs || !out_ids || !res))) return set_error(FLINNG_ERR_INVALID_ARG, "replay: null argument");
+    if (n > 0xFFFFFFFFull) return set_error(FLINNG_ERR_INVALID_ARG, "replay: more than 2^32 - 1 requests");
     const uint32_t km = srv->cfg.k_max;
     const Layout Lo = layout_for(srv);
     for (uint64_t i = 0; i < n; ++i) {
@@ -406,9 +424,12 @@ int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_
             const char *h = static_cast<const char *>(s.hstage);
             for (size_t i = 0; i < s.reqs.size(); ++i) {
                 const uint64_t r = s.reqs[i];
-                std::memcpy(out_ids + r * km, h + Lo.ids + i * km * sizeof(uint32_t), km * sizeof(uint32_t));
-                if (out_scores)
-                    std::memcpy(out_scores + r * km, h + Lo.sc + i * km * sizeof(uint16_t), km * sizeof(uint16_t));
+                if (!s.direct) {
+                    std::memcpy(out_ids + r * km, h + Lo.ids + i * km * sizeof(uint32_t), km * sizeof(uint32_t));
+                    if (out_scores)
+                        std::memcpy(out_scores + r * km, h + Lo.sc + i * km * sizeof(uint16_t),
+                                    km * sizeof(uint16_t));
+                }
                 res[r].t_done = t;
                 res[r].status = FLINNG_OK;
                 res[r].slot = uint32_t(si);
@@ -472,7 +493,7 @@ int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_
                     res[r].version = S.version;
                     res[r].batch = uint32_t(batches);
                 }
-                FL_TRY(launch_batch(srv, s, reqs));
+                FL_TRY(launch_batch(srv, s, reqs, out_ids, out_scores));
                 s.busy = true;
                 S.inflight++;
                 ++batches;
