@@ -50,6 +50,10 @@ sys.path.insert(0, ROOT)
 
 from paper_2106_11565_gb300 import workloads as WL  # noqa: E402
 
+# SRP arithmetic of cosine indices (library precision codes); the sign bits are exact in every one
+PRECISIONS = {"fp32": 0, "bf16x2": 1, "bf16": 2, "fp8": 3}
+PREC_NAMES = {0: "FP32 FFMA", 1: "BF16x2 tcgen05", 2: "BF16 tcgen05", 3: "FP8 E4M3 tcgen05 (row scales)"}
+
 METRIC = ("queries/s at recall@10≥0.9 on 1 GB300, serving vs plain form; "
           "p50/p99 latency")
 UNIT = "queries/s"
@@ -680,11 +684,15 @@ def recall_sweep(F, c: dict, name: str, prec: int, dev, d_pts, d_q, ex_ids, ex_s
 # CPU oracle timing
 # --------------------------------------------------------------------------
 
-def build_streamed(F, ix, c: dict, dev, d_perm):
+def build_streamed(F, ix, c: dict, dev, d_perm, hasher=None):
     """Build over the seeded embedding stream: generate a chunk on the device,
-    hash it (SRP GEMM), keep its buckets; then one flinng_build_buckets."""
+    hash it (SRP GEMM), keep its buckets; then one flinng_build_buckets.
+    ``hasher``: another index with the same projections whose precision
+    hashes the stream (the codes are exact in every precision, so the index
+    is the same)."""
     import torch
     L = c["L"]
+    hx = hasher if hasher is not None else ix
     all_b = torch.empty((c["N"], L), dtype=torch.int32, device=dev)
     xbuf = torch.empty((c["chunk"], c["d"]), dtype=torch.float32, device=dev)
     for first in range(0, c["N"], c["chunk"]):
@@ -692,7 +700,7 @@ def build_streamed(F, ix, c: dict, dev, d_perm):
         x = F.generate_embeddings(c["seed"], c["d"], c["n_centers"], c["sigma"], first, n, out=xbuf[:n])
         fp = F.flinng_points()
         fp.x, fp.ld = x.data_ptr(), c["d"]
-        F._check(ix.lib.flinng_hash(ix.h, C.byref(fp), n, all_b[first:first + n].data_ptr(), None, None, 1))
+        F._check(hx.lib.flinng_hash(hx.h, C.byref(fp), n, all_b[first:first + n].data_ptr(), None, None, 1))
     ix.build_buckets(all_b, d_perm)
     del all_b, xbuf
 
@@ -1145,8 +1153,8 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
         import torch.distributed as dist
     nq, k, L = c["nq"], c["k"], c["L"]
 
-    prec = F.PREC_BF16X2 if (args.precision == "bf16x2" and c["metric"] == "cosine") else F.PREC_FP32
-    prec_name = {F.PREC_FP32: "FP32 FFMA", F.PREC_BF16X2: "BF16x2 tcgen05"}[prec]
+    prec = PRECISIONS[args.precision] if c["metric"] == "cosine" else F.PREC_FP32
+    prec_name = PREC_NAMES[prec]
     ix = F.Index(c["metric"], c["R"], c["B"], L, c["K"], capacity=c["N"], params=c["params"],
                  dim=c.get("d", 0), W=c["W"], precision=prec)
 
@@ -1166,10 +1174,19 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
         d_q = F.generate_embeddings(c["seed"], c["d"], c["n_centers"], c["sigma"], 0, nq,
                                     queries=True, q_sigma=c["qsigma"], n_points=c["N"])
         c["d_q"] = d_q
+        # single-term forms re-check a large share of projections one by one
+        # (rigorous margins); the stream of 10^7 points is hashed by the
+        # two-term form instead: the codes, and so the index, are the same
+        hasher = None
+        if prec in (F.PREC_BF16, F.PREC_FP8):
+            hasher = F.Index(c["metric"], c["R"], c["B"], L, c["K"], capacity=1, params=c["params"],
+                             dim=c.get("d", 0), W=c["W"], precision=F.PREC_BF16X2)
+
         def build_once():
-            build_streamed(F, ix, c, dev, d_perm)
+            build_streamed(F, ix, c, dev, d_perm, hasher)
         n_builds, n_warm = 1, 0
-        build_note = (f"streamed: generate 32768-point chunks on the device, {prec_name} SRP GEMM, keep "
+        build_note = (f"streamed: generate 32768-point chunks on the device, "
+                      f"{PREC_NAMES[F.PREC_BF16X2] if hasher else prec_name} SRP GEMM, keep "
                       "buckets; then flinng_build_buckets (generation included)")
     else:
         d_pts = to_dev_points(c["pts"])
@@ -1355,17 +1372,22 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     h_mean = statistics.mean(hash_ms)
     big_srp = c["metric"] == "cosine" and c["L"] * c["K"] * c["d"] > (1 << 18)
     sm_max = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0)
-    if big_srp and h_mean > q_mean and prec == F.PREC_BF16X2:
-        # the dominant stage is the tensor-core SRP (split, tcgen05 GEMM, re-checks)
+    if big_srp and h_mean > q_mean and prec != F.PREC_FP32:
+        # the dominant stage is the tensor-core SRP (quantise, tcgen05 GEMM, re-checks)
         flops = 2.0 * nq * c["d"] * c["L"] * c["K"]
         achieved = flops / (h_mean / 1e3) / 1e12
-        peak = peaks.get("bf16_tflops", 1900.0)
-        roof = {"kernel": "k_srp_tc (+ k_split_rows, re-checks)", "bound": "tensor", "achieved": achieved,
+        bf16 = peaks.get("bf16_tflops", 1900.0)
+        fp8 = prec == F.PREC_FP8
+        peak = bf16 * (4.5 / 2.25 if fp8 else 1.0)
+        src = ("measured" if "bf16_tflops" in peaks else "fallback") + " bf16_tflops (burst)"
+        roof = {"kernel": "k_srp_tc (+ quantiser, re-checks)", "bound": "tensor", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "algorithmic_flops_per_launch": flops,
-                "issued_tensor_flops_per_launch": 3 * flops,
-                "peak_source": ("measured" if "bf16_tflops" in peaks else "fallback") + " bf16_tflops (burst)",
-                "note": "algorithmic FLOPs = 2 n d L K; the two-term split issues three BF16 MMAs per product"}
+                "issued_tensor_flops_per_launch": (3 if prec == F.PREC_BF16X2 else 1) * flops,
+                "peak_source": src + (" x 2 (nominal FP8 / BF16 dense ratio, 4.5 / 2.25 PFLOP/s)" if fp8 else ""),
+                "note": "algorithmic FLOPs = 2 n d L K; the two-term split issues three BF16 MMAs per product, "
+                        "the single-term forms one; the stage time includes the re-checks of projections "
+                        "inside the margin"}
     elif big_srp and h_mean > q_mean:
         # the timed step's dominant kernel is the FP32 SRP GEMM: FMA-pipe bound
         dom = "k_srp_fp32 (+ k_srp_recheck)"
@@ -1490,9 +1512,13 @@ def run_serving(args) -> dict:
     # embedding index (streamed build)
     ix4 = F.Index("cosine", c4["R"], c4["B"], c4["L"], c4["K"], capacity=c4["N"], params=c4["params"],
                   dim=c4["d"], W=c4["W"],
-                  precision=F.PREC_BF16X2 if args.precision == "bf16x2" else F.PREC_FP32)
+                  precision=PRECISIONS[args.precision])
+    hasher = None
+    if PRECISIONS[args.precision] in (F.PREC_BF16, F.PREC_FP8):
+        hasher = F.Index("cosine", c4["R"], c4["B"], c4["L"], c4["K"], capacity=1, params=c4["params"],
+                         dim=c4["d"], W=c4["W"], precision=F.PREC_BF16X2)
     t0 = time.perf_counter()
-    build_streamed(F, ix4, c4, dev, torch.from_numpy(c4["perm"].view(np.int32)).to(dev))
+    build_streamed(F, ix4, c4, dev, torch.from_numpy(c4["perm"].view(np.int32)).to(dev), hasher)
     torch.cuda.synchronize()
     build4_s = time.perf_counter() - t0
     q4 = F.generate_embeddings(c4["seed"], c4["d"], c4["n_centers"], c4["sigma"], 0, c4["nq"], queries=True,
@@ -1575,7 +1601,7 @@ def run_serving(args) -> dict:
                    "form": "serving: continuous batching, 8 streams, batches <= 1024, host buffers in and out",
                    "rates": "0.25x, 0.5x, 0.9x and 2.0x (overload) of the plain form's mixed throughput",
                    "hbm_budget_bytes": int(ix2.device_bytes + ix4.device_bytes + (4 << 30)),
-                   "srp_precision": "BF16x2 tcgen05" if args.precision == "bf16x2" else "FP32 FFMA"},
+                   "srp_precision": PREC_NAMES[PRECISIONS[args.precision]]},
         "plain_form": {"mixed_qps": plain_mix, "C2_qps": plain["C2"]["qps"], "C4_qps": plain["C4"]["qps"],
                        "note": "hash kernel then count/decode/top-k kernel, whole query batch of each index "
                                "resident in HBM, per-query k uniform in {1,10,100} as served"},
@@ -1642,7 +1668,7 @@ def main():
     ap.add_argument("--configured", action="store_true",
                     help="time the fused form at the parameters the workload's config names instead of the "
                          "serving form at the recall-target parameters (the default where those are known)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x2"],
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS),
                     help="SRP projection arithmetic for cosine workloads (signs are exact either way)")
     args = ap.parse_args()
     if args.warmup < 3:

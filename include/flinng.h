@@ -69,6 +69,17 @@ extern "C" {
                                   pipeline waits are bounded: a wait that gave up (never expected)
                                   makes the index's next hash or query, and flinng_hash_counters,
                                   return FLINNG_ERR_TIMEOUT from then on */
+#define FLINNG_PREC_BF16 2     /* tensor cores (tcgen05), one bf16 term per operand, fp32 accumulation;
+                                  the margin is a-posteriori: it uses each row's own quantisation
+                                  residual norm ||x - bf16(x)|| (and the same for every projection
+                                  row), so it is rigorous yet follows the data; needs dim % 8 == 0 */
+#define FLINNG_PREC_FP8 3      /* tensor cores (tcgen05 kind::f8f6f4), FP8 E4M3 operands with a
+                                  power-of-two scale per row (values that would be E4M3 subnormals
+                                  become 0), fp32 accumulation, the same a-posteriori margin; needs
+                                  dim % 16 == 0. With every tensor-core form, projections inside the
+                                  margin go to compensated fp32, then fp64 / exact re-checks, so the
+                                  codes are those of FLINNG_PREC_FP32; the waits are bounded as
+                                  for FLINNG_PREC_BF16X2 */
 
 typedef struct flinng_config {
     uint32_t metric;        /* FLINNG_COSINE_SRP or FLINNG_JACCARD_DOPH */
@@ -82,7 +93,7 @@ typedef struct flinng_config {
                                1..30 with L * 2^W < 2^31 */
     uint32_t min_threshold; /* t_min >= 1: cells with fewer collisions never test
                                positive (Sec. 5 threshold t, relaxed by Alg. 3) */
-    uint32_t precision;     /* FLINNG_PREC_FP32 or FLINNG_PREC_BF16X2 (cosine) */
+    uint32_t precision;     /* FLINNG_PREC_FP32, _BF16X2, _BF16 or _FP8 (cosine) */
     uint32_t reserved;
     uint64_t capacity;      /* maximum number of points, inserts included;
                                L * R * capacity < 2^32 */
@@ -364,9 +375,10 @@ uint64_t flinng_kernel_launches(void);
  * out_ids and out_scores are device memory; the call is asynchronous on the
  * index's stream. The index's device must be the current device.
  * Limits: nq * L <= 262144, and for cosine indices nq * L * K <= 655296.
- * Cosine indices of precision FLINNG_PREC_BF16X2 also stage the two bf16
- * parts of every query row and two re-check lists in the same 5 MiB part of
- * the array: about nq * (4 * dim + 16 * L * K + 4) + 8192 <= 5242880 bytes
+ * Cosine indices of a tensor-core precision also stage every query row's
+ * quantised parts (at most 4 * dim bytes: FLINNG_PREC_BF16X2) and two
+ * re-check lists in the same 5 MiB part of
+ * the array: about nq * (4 * dim + 16 * L * K + 12) + 8192 <= 5242880 bytes
  * (the call computes the exact figure). Larger batches are rejected with
  * FLINNG_ERR_INVALID_ARG before anything runs (split them, or use
  * flinng_query).

@@ -96,7 +96,7 @@ void free_index(flinng_index *ix)
     void *ptrs[] = {ix->srp_w, ix->bucket_a, ix->bucket_c, ix->gid, ix->moff, ix->mem, ix->mrec, ix->off,
                     ix->hidx, ix->hbm,
                     ix->cells, ix->cells_tmp, ix->slot_a, ix->slot_b, ix->cell_cnt, ix->flag, ix->qnext,
-                    ix->stats, ix->ws.ptr, ix->w_split, ix->w_norm, ix->tc_err};
+                    ix->stats, ix->ws.ptr, ix->w_split, ix->w_norm, ix->w_aux, ix->tc_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ix->h_flag) cudaFreeHost(ix->h_flag);
@@ -117,10 +117,14 @@ int check_config(const flinng_config *c, const flinng_params *p)
         return set_error(FLINNG_ERR_INVALID_ARG, "create: need 1 <= W <= 30 and L*2^W < 2^31");
     if (c->min_threshold < 1 || c->min_threshold > c->L)
         return set_error(FLINNG_ERR_INVALID_ARG, "create: min_threshold must be in 1..L");
-    if (c->precision != FLINNG_PREC_FP32 && c->precision != FLINNG_PREC_BF16X2)
+    if (c->precision > FLINNG_PREC_FP8)
         return set_error(FLINNG_ERR_INVALID_ARG, "create: unsupported precision %u", c->precision);
-    if (c->precision == FLINNG_PREC_BF16X2 && (c->metric != FLINNG_COSINE_SRP || c->dim % 8 != 0))
-        return set_error(FLINNG_ERR_INVALID_ARG, "create: the tensor-core precision needs cosine and dim % 8 == 0");
+    if (c->precision != FLINNG_PREC_FP32 && c->metric != FLINNG_COSINE_SRP)
+        return set_error(FLINNG_ERR_INVALID_ARG, "create: the tensor-core precisions are for cosine indices");
+    if ((c->precision == FLINNG_PREC_BF16X2 || c->precision == FLINNG_PREC_BF16) && c->dim % 8 != 0)
+        return set_error(FLINNG_ERR_INVALID_ARG, "create: the BF16 tensor-core precisions need dim % 8 == 0");
+    if (c->precision == FLINNG_PREC_FP8 && c->dim % 16 != 0)
+        return set_error(FLINNG_ERR_INVALID_ARG, "create: the FP8 tensor-core precision needs dim % 16 == 0");
     if (c->capacity < 1 || uint64_t(c->L) * c->R * c->capacity >= (1ull << 32))
         return set_error(FLINNG_ERR_INVALID_ARG, "create: need capacity >= 1 and L*R*capacity < 2^32");
     if (c->metric == FLINNG_COSINE_SRP) {
@@ -427,7 +431,7 @@ int flinng_create(const flinng_config *cfg, const flinng_params *params, void *s
         chk(cudaMemsetAsync(ix->moff, 0, (size_t(ix->BR) + 1) * sizeof(uint32_t), st), "zero moff");
         chk(cudaMemsetAsync(ix->stats, 0, kStats * sizeof(unsigned long long), st), "zero stats");
         chk(cudaMemsetAsync(ix->tc_err, 0, 4, st), "zero tensor-core flag");
-        if (rc == FLINNG_OK && cfg->precision == FLINNG_PREC_BF16X2) rc = srp_tc_prepare_weights(ix);
+        if (rc == FLINNG_OK && cfg->precision != FLINNG_PREC_FP32) rc = srp_tc_prepare_weights(ix);
         chk(cudaStreamSynchronize(st), "create sync");
     }
     if (rc != FLINNG_OK) {

@@ -106,7 +106,7 @@ extern "C" int flinng_query_noalloc(flinng_index *idx, const flinng_points *q, u
                          "query_noalloc: nq * L = %llu exceeds the limit of %llu (fixed scratch)",
                          (unsigned long long)(uint64_t(nq) * idx->cfg.L),
                          (unsigned long long)(kBucketBytes / sizeof(uint32_t)));
-    if (srp && idx->cfg.precision == FLINNG_PREC_BF16X2 && srp_workspace_bytes(idx, nq) > kHashBytes)
+    if (srp && idx->cfg.precision != FLINNG_PREC_FP32 && srp_workspace_bytes(idx, nq) > kHashBytes)
         return set_error(FLINNG_ERR_INVALID_ARG,
                          "query_noalloc: batch of %u needs %zu bytes of tensor-core scratch (limit %zu)", nq,
                          srp_workspace_bytes(idx, nq), kHashBytes);

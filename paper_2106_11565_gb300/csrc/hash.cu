@@ -293,7 +293,7 @@ int srp_recheck_list(flinng_index *ix, const float *x, uint64_t ld, const unsign
 
 size_t srp_workspace_bytes(const flinng_index *ix, uint64_t n)
 {
-    if (ix->cfg.precision == FLINNG_PREC_BF16X2) return srp_tc_workspace_bytes(ix, n);
+    if (ix->cfg.precision != FLINNG_PREC_FP32) return srp_tc_workspace_bytes(ix, n);
     const uint64_t rows = n < uint64_t(kSrpChunkRows) ? n : uint64_t(kSrpChunkRows);
     return carve_bytes<unsigned long long>(2) + carve_bytes<unsigned long long>(rows * ix->P + 1);
 }
@@ -302,7 +302,7 @@ int srp_hash(flinng_index *ix, const float *x, uint64_t ld, uint64_t n,
              uint32_t *buckets, float *proj, void *ws, size_t ws_bytes)
 {
     (void)ws_bytes;
-    if (ix->cfg.precision == FLINNG_PREC_BF16X2) return srp_hash_tc(ix, x, ld, n, buckets, proj, ws);
+    if (ix->cfg.precision != FLINNG_PREC_FP32) return srp_hash_tc(ix, x, ld, n, buckets, proj, ws);
     const cudaStream_t st = ix->stream;
     const uint32_t L = ix->cfg.L, K = ix->cfg.K, d = ix->cfg.dim, P = ix->P;
     Carver c(ws, ~size_t(0));

@@ -105,6 +105,7 @@ struct flinng_index {
     double srp_gamma64;       // 2 * gamma_d for the fp64 recheck
     void *w_split;            // tensor-core precision: bf16 w1 then w2, P x dim each
     float *w_norm;            // upper bounds of ||w_j||
+    float *w_aux;             // single-term tensor forms: P upper bounds of ||w_j - q(w_j)||, then P row scales
     uint32_t *tc_err;         // tensor-core pipeline timeout flag
 
     // shape

@@ -134,7 +134,7 @@ Layout layout_for(const flinng_server *srv)
     L.in_el = (size_t)c.take<uint32_t>(in_floats > in_elems ? in_floats : in_elems);
     L.qb = (size_t)c.take<uint32_t>(nb * srv->max_L);
     // re-check lists (fp32 path) or the tensor-core split operands and lists
-    L.srp = (size_t)c.take<unsigned long long>(2 * nb * srv->max_P + 64 + nb * srv->max_dim / 2 + nb + 1024);
+    L.srp = (size_t)c.take<unsigned long long>(2 * nb * srv->max_P + 64 + nb * srv->max_dim / 2 + 2 * nb + 1024);
     L.ids = (size_t)c.take<uint32_t>(nb * km);
     L.sc = (size_t)c.take<uint16_t>(nb * km);
     L.total = c.used + 256;

@@ -19,14 +19,31 @@
 // two-sum), and the few that stay ambiguous to the fp64 / exact re-check of
 // hash.cu.
 //
+// Single-term forms. FLINNG_PREC_BF16 keeps x1 = bf16(x) only; FLINNG_PREC_FP8
+// keeps xq = e4m3(x / s) with a power-of-two scale s per row (s chosen so the
+// row's largest |x| / s <= 448; values that would be E4M3 subnormals become
+// 0). The quantiser records each row's residual norm ||e_x|| = ||x - s xq||
+// (exact fp64 differences, rounded up); with ||x|| and the same for every
+// projection row w,
+//   |w.x - s_x s_w sum xq wq| <= ||x|| ||e_w|| + ||e_x|| ||w|| + 3 ||e_x|| ||e_w||
+// (Cauchy-Schwarz on x = s_x xq + e_x, w = s_w wq + e_w). The tensor cores sum
+// the products of one k-block (64 bf16 or 128 e4m3 values) exactly-multiplied
+// into fp32 (per-product error u' = 2^-22 of the running magnitude), the
+// epilogue adds the blocks in fp32 and scales by s_x s_w (exact), so the
+// margin is that residual term plus [g'(kb) + g(m)(1 + g'(kb))] (||x|| +
+// ||e_x||) (||w|| + ||e_w||), 2^-23 |p~|, the underflow terms above, and a
+// 2^-20 relative slack for evaluating the margin itself in fp32.
+//
 // Kernel layout (one CTA per 128 points x 128 projections, 320 threads):
 //   warp 0     TMA producer: 3-stage ring of {X1, X2, W1, W2} tiles of 128 rows
-//              x 64 bf16 (128-byte swizzle), one mbarrier per stage;
+//              x 64 bf16 (128-byte swizzle), one mbarrier per stage (single-term
+//              forms: a 6-stage ring of {X, W} tiles of 128 rows x 128 bytes);
 //   warp 1     allocates 512 TMEM columns (two buffers of {hi, lo}); one elected
 //              thread issues the MMAs of k-block s into buffer s % 2 - per 16-wide
 //              step x1 [w1 w2] (M=128, N=256: hi and the x1 w2 half of lo) and
 //              x2 w1 (N=128, into lo) - then commits the stage back to the
-//              producer and the buffer to the epilogue;
+//              producer and the buffer to the epilogue (single-term forms: one
+//              N=128 MMA per 32-byte step into a 128-column buffer);
 //   warps 2-9  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +32 (one point per
 //              thread) and 64 of the 128 columns, drains each buffer into fp32
 //              registers and hands it back; at the end decides the signs,
@@ -35,17 +52,33 @@
 // stops issuing work, waits (bounded) for its copies and MMAs, and frees TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "internal.cuh"
 
 namespace flinng {
 namespace {
 
-constexpr int kTM = 128, kTN = 128, kTK = 64;     // tile rows, projections, K per stage
-constexpr int kStages = 3;
-constexpr int kTileBytes = kTM * kTK * 2;         // 16 KB per operand tile
-constexpr int kStageBytes = 4 * kTileBytes;       // X1, X2, W1, W2
-constexpr uint32_t kTmemCols = 512;               // buffer b: hi at 256 b, lo at 256 b + 128
+constexpr int kTM = 128, kTN = 128, kTK = 64;     // tile rows, projections, bf16 K per stage
+constexpr int kTileBytes = kTM * 128;             // 16 KB per operand tile (128-byte rows)
+// forms of the kernel
+constexpr int kFormBf16x2 = 0, kFormBf16 = 1, kFormFp8 = 2;
+
+template <int FORM> struct TcForm;
+template <> struct TcForm<kFormBf16x2> {
+    static constexpr int kTiles = 4, kStages = 3, kKElems = 64;   // X1, X2, W1, W2
+    static constexpr uint32_t kTmemCols = 512;                    // buffer b: hi at 256 b, lo at 256 b + 128
+};
+template <> struct TcForm<kFormBf16> {
+    static constexpr int kTiles = 2, kStages = 6, kKElems = 64;   // X, W
+    static constexpr uint32_t kTmemCols = 256;                    // buffer b at 128 b
+};
+template <> struct TcForm<kFormFp8> {
+    static constexpr int kTiles = 2, kStages = 6, kKElems = 128;
+    static constexpr uint32_t kTmemCols = 256;
+};
+template <int FORM>
+constexpr size_t tc_smem_bytes() { return size_t(TcForm<FORM>::kStages) * TcForm<FORM>::kTiles * kTileBytes + 1024 + 256; }
 constexpr int kEpiWarps = 8;                      // two per TMEM lane quarter, 64 columns each
 constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 constexpr uint64_t kWaitNs = 1000000000ull;       // bounded mbarrier waits: 1 s
@@ -139,6 +172,25 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         : "memory");
 }
 
+// Instruction descriptor, kind::f8f6f4: D fp32, A and B E4M3 (format 0), both
+// K-major, M = 128 rows, N columns.
+template <int N>
+__host__ __device__ constexpr uint32_t mma_idesc_e4m3()
+{
+    return (1u << 4) | (uint32_t(N >> 3) << 17) | (uint32_t(kTM >> 4) << 24);
+}
+
+template <int N>
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(mma_idesc_e4m3<N>()), "r"(accumulate)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -170,6 +222,10 @@ struct TcArgs {
     uint32_t P, d, L, K;
     const float *xnorm;    // n: upper bounds of ||x||
     const float *wnorm;    // P: upper bounds of ||w||
+    const float *xres;     // single-term forms: n upper bounds of ||x - s_x xq||
+    const float *wres;     // P upper bounds of ||w - s_w wq||
+    const float *xscale;   // FP8: n row scales s_x (powers of two)
+    const float *wscale;   // FP8: P row scales s_w
     float c_norm;          // margin factor on ||x|| ||w||
     float c_sub;           // margin factor on ||x|| + ||w|| (subnormal flushes)
     float tiny;            // absolute margin (underflow)
@@ -185,10 +241,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+template <int FORM>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtensorMap mx2,
          const __grid_constant__ CUtensorMap mw1, const __grid_constant__ CUtensorMap mw2, TcArgs a)
 {
+    using F = TcForm<FORM>;
+    constexpr int kStages = F::kStages;
+    constexpr int kStageBytes = F::kTiles * kTileBytes;
+    constexpr int kW = F::kTiles / 2;                 // tile index of the first W tile in a stage
+    constexpr uint32_t kBuf = F::kTmemCols / 2;        // TMEM columns per buffer
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     // 1024-byte aligned tile ring, then barriers and the TMEM address
     unsigned char *ring = tc_smem + ((1024u - (smem_u32(tc_smem) & 1023u)) & 1023u);
@@ -204,7 +266,7 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
     // projection blocks vary fastest: the CTAs that share one X tile run in
     // the same wave, so X is read from DRAM once and W stays in L2
     const uint32_t row0 = blockIdx.y * kTM, col0 = blockIdx.x * kTN;
-    const uint32_t nkb = (a.d + kTK - 1) / kTK;
+    const uint32_t nkb = (a.d + F::kKElems - 1) / F::kKElems;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -222,7 +284,7 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(tmem_slot)), "r"(kTmemCols) : "memory");
+                     ::"r"(smem_u32(tmem_slot)), "r"(F::kTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -242,11 +304,11 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
                 if (*(volatile uint32_t *)abort_flag) break;
                 unsigned char *st = ring + s * kStageBytes;
                 mbar_expect_tx(&full[s], kStageBytes);
-                const int kx = int(kb * kTK);
+                const int kx = int(kb * F::kKElems);
                 tma_load_2d(st + 0 * kTileBytes, &mx1, &full[s], kx, int(row0));
-                tma_load_2d(st + 1 * kTileBytes, &mx2, &full[s], kx, int(row0));
-                tma_load_2d(st + 2 * kTileBytes, &mw1, &full[s], kx, int(col0));
-                tma_load_2d(st + 3 * kTileBytes, &mw2, &full[s], kx, int(col0));
+                if constexpr (F::kTiles == 4) tma_load_2d(st + 1 * kTileBytes, &mx2, &full[s], kx, int(row0));
+                tma_load_2d(st + kW * kTileBytes, &mw1, &full[s], kx, int(col0));
+                if constexpr (F::kTiles == 4) tma_load_2d(st + 3 * kTileBytes, &mw2, &full[s], kx, int(col0));
                 issued = kb + 1;
             }
         }
@@ -263,19 +325,27 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
                 if (*(volatile uint32_t *)abort_flag) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t st = smem_u32(ring + s * kStageBytes);
-                const uint32_t t_hi = tmem + 256u * b, t_lo = t_hi + kTN;
-                // W1 and W2 tiles are adjacent in the stage, so [W1; W2] is one
-                // 256-row B operand: x1 [w1 w2] fills hi and lo in one MMA
-                // (N = 256), then x2 w1 adds into lo (N = 128)
+                const uint32_t t_hi = tmem + kBuf * b;
+                // four 32-byte K steps per 128-byte stage row: 16 bf16 or 32 e4m3
 #pragma unroll
-                for (int kk = 0; kk < kTK / 16; ++kk) {
+                for (int kk = 0; kk < 4; ++kk) {
                     const uint32_t off = kk * 32;
-                    const uint64_t x1 = smem_desc(st + 0 * kTileBytes + off);
-                    const uint64_t x2 = smem_desc(st + 1 * kTileBytes + off);
-                    const uint64_t w12 = smem_desc(st + 2 * kTileBytes + off);
-                    const uint32_t acc = kk > 0 ? 1u : 0u;     // each k-block starts a fresh pair
-                    mma_bf16<2 * kTN>(t_hi, x1, w12, acc);
-                    mma_bf16<kTN>(t_lo, x2, w12, 1u);
+                    const uint32_t acc = kk > 0 ? 1u : 0u;     // each k-block starts a fresh accumulator
+                    if constexpr (FORM == kFormBf16x2) {
+                        // W1 and W2 tiles are adjacent in the stage, so [W1; W2] is one
+                        // 256-row B operand: x1 [w1 w2] fills hi and lo in one MMA
+                        // (N = 256), then x2 w1 adds into lo (N = 128)
+                        const uint64_t x1 = smem_desc(st + 0 * kTileBytes + off);
+                        const uint64_t x2 = smem_desc(st + 1 * kTileBytes + off);
+                        const uint64_t w12 = smem_desc(st + 2 * kTileBytes + off);
+                        mma_bf16<2 * kTN>(t_hi, x1, w12, acc);
+                        mma_bf16<kTN>(t_hi + kTN, x2, w12, 1u);
+                    } else {
+                        const uint64_t xd = smem_desc(st + off);
+                        const uint64_t wd = smem_desc(st + kTileBytes + off);
+                        if constexpr (FORM == kFormBf16) mma_bf16<kTN>(t_hi, xd, wd, acc);
+                        else mma_e4m3<kTN>(t_hi, xd, wd, acc);
+                    }
                 }
                 mma_commit(&empty[s]);
                 mma_commit(&tfull[b]);
@@ -303,39 +373,68 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // two halves of 32 columns: hi and lo loads in flight together, one
-            // wait each; the buffer goes back to the MMA issuer before the
-            // second half is added
-            uint32_t hv[32], lv[32];
-            tmem_ld32(tbase + 256u * b, hv);
-            tmem_ld32(tbase + 256u * b + kTN, lv);
-            tmem_wait_ld();
+            if constexpr (FORM == kFormBf16x2) {
+                // two halves of 32 columns: hi and lo loads in flight together, one
+                // wait each; the buffer goes back to the MMA issuer before the
+                // second half is added
+                uint32_t hv[32], lv[32];
+                tmem_ld32(tbase + kBuf * b, hv);
+                tmem_ld32(tbase + kBuf * b + kTN, lv);
+                tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(hv[j]) + __uint_as_float(lv[j]);
-            tmem_ld32(tbase + 256u * b + 32, hv);
-            tmem_ld32(tbase + 256u * b + kTN + 32, lv);
-            tmem_wait_ld();
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
+                for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(hv[j]) + __uint_as_float(lv[j]);
+                tmem_ld32(tbase + kBuf * b + 32, hv);
+                tmem_ld32(tbase + kBuf * b + kTN + 32, lv);
+                tmem_wait_ld();
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc[32 + j] += __uint_as_float(hv[j]) + __uint_as_float(lv[j]);
+                for (int j = 0; j < 32; ++j) acc[32 + j] += __uint_as_float(hv[j]) + __uint_as_float(lv[j]);
+            } else {
+                uint32_t hv[32], hw[32];
+                tmem_ld32(tbase + kBuf * b, hv);
+                tmem_ld32(tbase + kBuf * b + 32, hw);
+                tmem_wait_ld();
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    acc[j] += __uint_as_float(hv[j]);
+                    acc[32 + j] += __uint_as_float(hw[j]);
+                }
+            }
         }
         uint32_t ab = lane == 0 ? *(volatile uint32_t *)abort_flag : 0u;
         abort = abort || __shfl_sync(0xffffffffu, ab, 0) != 0u;    // warp-uniform
         const uint64_t row = uint64_t(row0) + quarter + lane;
         if (!abort && row < a.n) {
             const float xn = a.xnorm[row];
+            float xr = 0.f, xs = 1.f;
+            if constexpr (FORM != kFormBf16x2) xr = a.xres[row];
+            if constexpr (FORM == kFormFp8) xs = a.xscale[row];
             uint32_t cur_l = 0xFFFFFFFFu, cur_bits = 0u;
 #pragma unroll
             for (int j = 0; j < 64; ++j) {
                 const uint32_t col = col0 + 64u * half + j;
                 if (col >= a.P) break;
-                const float p = acc[j];
+                float p = acc[j];
+                if constexpr (FORM == kFormFp8) p *= xs * a.wscale[col];    // powers of two: exact
                 const float wn = a.wnorm[col];
                 if (a.proj) a.proj[row * a.P + col] = p;
-                const float margin =
-                    fmaf(a.c_norm * xn, wn, fmaf(ldexpf(1.f, -23), fabsf(p), fmaf(a.c_sub, xn + wn, a.tiny)));
+                float margin;
+                if constexpr (FORM == kFormBf16x2) {
+                    margin = fmaf(a.c_norm * xn, wn, fmaf(ldexpf(1.f, -23), fabsf(p), fmaf(a.c_sub, xn + wn, a.tiny)));
+                } else {
+                    // residual term (Cauchy-Schwarz on the quantisation errors) plus
+                    // accumulation on the quantised operands' norms, then slack
+                    const float wr = a.wres[col];
+                    const float resid = fmaf(xn, wr, fmaf(xr, wn, 3.f * xr * wr));
+                    const float accum = a.c_norm * (xn + xr) * (wn + wr);
+                    margin = (resid + accum + fmaf(ldexpf(1.f, -23), fabsf(p), fmaf(a.c_sub, xn + wn, a.tiny))) *
+                             (1.f + ldexpf(1.f, -20));
+                }
                 if (fabsf(p) > margin) {
                     if (p > 0.f) {
                         const uint32_t l = col / a.K;
@@ -369,7 +468,7 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
         if (lane == 0) mbar_wait(mdone, 0);
         __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(F::kTmemCols) : "memory");
     }
     __syncthreads();
 }
@@ -396,6 +495,69 @@ __global__ void k_split_rows(const float *__restrict__ x, uint64_t ld, uint64_t 
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         // fp64 sum of d squares, sqrt, rounded up with room to spare
         if (lane == 0) norm[r] = __double2float_ru(sqrt(ss * (1.0 + 1e-12)) * (1.0 + 1e-7));
+    }
+}
+
+// Single-term quantisers: q = bf16(x) (FORM kFormBf16) or q = e4m3(x / s) with
+// s = 2^e, e the smallest with max |x| / s < 448 (FORM kFormFp8; a value whose
+// quantised magnitude would be below 2^-6, an E4M3 subnormal, becomes 0). Per
+// row: upper bounds of ||x|| and of ||x - s q|| (exact fp64 differences, fp64
+// sums of squares, rounded up), and s.
+template <int FORM>
+__global__ void k_quant_rows(const float *__restrict__ x, uint64_t ld, uint64_t n, uint32_t d,
+                             void *__restrict__ q, float *__restrict__ norm, float *__restrict__ res,
+                             float *__restrict__ scale)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t gw = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t r = gw; r < n; r += nw) {
+        const float *xr = x + r * ld;
+        float s = 1.f;
+        if constexpr (FORM == kFormFp8) {
+            float mx = 0.f;
+            for (uint32_t t = lane; t < d; t += 32) mx = fmaxf(mx, fabsf(xr[t]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (mx > 0.f) {
+                int e;
+                frexpf(mx / 448.f, &e);      // mx / 448 = f 2^e with f in [0.5, 1): mx / 2^e < 448
+                s = ldexpf(1.f, e);
+            }
+        }
+        double ss = 0.0, rr = 0.0;
+        for (uint32_t t = lane; t < d; t += 32) {
+            const float v = xr[t];
+            float back;
+            if constexpr (FORM == kFormBf16) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                static_cast<__nv_bfloat16 *>(q)[r * d + t] = h;
+                back = __bfloat162float(h);
+            } else {
+                __nv_fp8_e4m3 h(v / s);                       // round to nearest, saturating
+                float hf = float(h);
+                if (fabsf(hf) < ldexpf(1.f, -6)) {
+                    h = __nv_fp8_e4m3(0.f);
+                    hf = 0.f;
+                }
+                static_cast<__nv_fp8_e4m3 *>(q)[r * d + t] = h;
+                back = hf * s;                                // exact: s is a power of two
+            }
+            const double e = double(v) - double(back);        // exact in fp64
+            ss += double(v) * double(v);
+            rr += e * e;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            rr += __shfl_xor_sync(0xffffffffu, rr, o);
+        }
+        if (lane == 0) {
+            // fp64 sums of d squares, sqrt, rounded up with room to spare
+            norm[r] = __double2float_ru(sqrt(ss * (1.0 + 1e-12)) * (1.0 + 1e-7));
+            res[r] = __double2float_ru(sqrt(rr * (1.0 + 1e-12)) * (1.0 + 1e-7));
+            if (scale) scale[r] = s;
+        }
     }
 }
 
@@ -476,18 +638,21 @@ int get_encoder(EncodeTiled *fn)
     return FLINNG_OK;
 }
 
-// 2-D bf16 map over rows x d (d contiguous, row stride d elements), box 64 x 128.
-int make_map(CUtensorMap *m, const void *base, uint64_t rows, uint32_t d)
+// 2-D map over rows x d (d contiguous, row stride d elements) of bf16 or
+// 8-bit elements; the box is 128 bytes (64 bf16 or 128 e4m3) x 128 rows.
+int make_map(CUtensorMap *m, const void *base, uint64_t rows, uint32_t d, bool bytes)
 {
     EncodeTiled enc = nullptr;
     FL_TRY(get_encoder(&enc));
+    const uint32_t esz = bytes ? 1u : 2u;
     const cuuint64_t dims[2] = {d, rows};
-    const cuuint64_t strides[1] = {uint64_t(d) * 2};
-    const cuuint32_t box[2] = {uint32_t(kTK), uint32_t(kTM)};
+    const cuuint64_t strides[1] = {uint64_t(d) * esz};
+    const cuuint32_t box[2] = {128u / esz, uint32_t(kTM)};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const CUresult r = enc(m, bytes ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                           const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(FLINNG_ERR_INVALID_ARG, "tensor map: error %d (d=%u)", int(r), d);
     return FLINNG_OK;
 }
@@ -499,26 +664,65 @@ inline unsigned warp_grid(uint64_t items)
     return (unsigned)(b ? b : 1);
 }
 
-}  // namespace
-
-int srp_tc_prepare_weights(flinng_index *ix)
+// bytes of one quantised row
+inline size_t qrow_bytes(uint32_t precision, uint32_t d)
 {
-    const uint32_t P = ix->P, d = ix->cfg.dim;
-    if (d % 8 != 0) return set_error(FLINNG_ERR_INVALID_ARG, "BF16 tensor-core SRP needs dim to be a multiple of 8");
-    FL_CUDA(cudaMalloc(&ix->w_split, size_t(P) * d * 2 * sizeof(__nv_bfloat16)));
-    FL_CUDA(cudaMalloc(&ix->w_norm, size_t(P) * sizeof(float)));
-    ix->device_bytes += size_t(P) * d * 4 + size_t(P) * 4;
-    __nv_bfloat16 *w1 = static_cast<__nv_bfloat16 *>(ix->w_split);
-    k_split_rows<<<warp_grid(P), 256, 0, ix->stream>>>(ix->srp_w, d, P, d, w1, w1 + size_t(P) * d, ix->w_norm);
+    return precision == FLINNG_PREC_BF16X2 ? size_t(d) * 4 : precision == FLINNG_PREC_BF16 ? size_t(d) * 2 : size_t(d);
+}
+
+int quant_rows(uint32_t precision, const float *x, uint64_t ld, uint64_t n, uint32_t d, void *q, float *norm,
+               float *res, float *scale, cudaStream_t st)
+{
+    if (precision == FLINNG_PREC_BF16X2) {
+        __nv_bfloat16 *q1 = static_cast<__nv_bfloat16 *>(q);
+        k_split_rows<<<warp_grid(n), 256, 0, st>>>(x, ld, n, d, q1, q1 + n * d, norm);
+    } else if (precision == FLINNG_PREC_BF16) {
+        k_quant_rows<kFormBf16><<<warp_grid(n), 256, 0, st>>>(x, ld, n, d, q, norm, res, nullptr);
+    } else {
+        k_quant_rows<kFormFp8><<<warp_grid(n), 256, 0, st>>>(x, ld, n, d, q, norm, res, scale);
+    }
     count_launch();
     FL_CUDA(cudaGetLastError());
     return FLINNG_OK;
 }
 
+template <int FORM>
+int launch_tc(const CUtensorMap &mx1, const CUtensorMap &mx2, const CUtensorMap &mw1, const CUtensorMap &mw2,
+              const TcArgs &a, uint64_t rows, cudaStream_t st)
+{
+    const size_t smem = tc_smem_bytes<FORM>();
+    FL_TRY(ensure_dyn_smem((const void *)k_srp_tc<FORM>, smem));
+    dim3 grid((a.P + kTN - 1) / kTN, (unsigned)((rows + kTM - 1) / kTM));
+    k_srp_tc<FORM><<<grid, kTcThreads, smem, st>>>(mx1, mx2, mw1, mw2, a);
+    count_launch();
+    FL_CUDA(cudaGetLastError());
+    return FLINNG_OK;
+}
+
+}  // namespace
+
+int srp_tc_prepare_weights(flinng_index *ix)
+{
+    const uint32_t P = ix->P, d = ix->cfg.dim, prec = ix->cfg.precision;
+    if (d % (prec == FLINNG_PREC_FP8 ? 16 : 8) != 0)
+        return set_error(FLINNG_ERR_INVALID_ARG, "tensor-core SRP: dim %u is not a multiple of %d", d,
+                         prec == FLINNG_PREC_FP8 ? 16 : 8);
+    const size_t qb = qrow_bytes(prec, d) * P;
+    FL_CUDA(cudaMalloc(&ix->w_split, qb));
+    FL_CUDA(cudaMalloc(&ix->w_norm, size_t(P) * sizeof(float)));
+    ix->device_bytes += qb + size_t(P) * 4;
+    if (prec != FLINNG_PREC_BF16X2) {
+        FL_CUDA(cudaMalloc(&ix->w_aux, size_t(P) * 2 * sizeof(float)));
+        ix->device_bytes += size_t(P) * 8;
+    }
+    return quant_rows(prec, ix->srp_w, d, P, d, ix->w_split, ix->w_norm, ix->w_aux, ix->w_aux ? ix->w_aux + P : nullptr,
+                      ix->stream);
+}
+
 size_t srp_tc_workspace_bytes(const flinng_index *ix, uint64_t n)
 {
     const uint64_t rows = n < kTcChunkRows ? n : kTcChunkRows;
-    return carve_bytes<__nv_bfloat16>(rows * ix->cfg.dim * 2) + carve_bytes<float>(rows) +
+    return carve_bytes<char>(rows * qrow_bytes(ix->cfg.precision, ix->cfg.dim)) + 3 * carve_bytes<float>(rows) +
            carve_bytes<unsigned long long>(8) + 2 * carve_bytes<unsigned long long>(rows * ix->P + 1) + 4096;
 }
 
@@ -529,45 +733,50 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
     // a wait that timed out in an earlier call (the flag is sticky on the device)
     if (ix->h_flag[3]) return set_error(FLINNG_ERR_TIMEOUT, "tensor-core SRP: a pipeline wait timed out");
     const cudaStream_t st = ix->stream;
-    const uint32_t L = ix->cfg.L, K = ix->cfg.K, d = ix->cfg.dim, P = ix->P;
+    const uint32_t L = ix->cfg.L, K = ix->cfg.K, d = ix->cfg.dim, P = ix->P, prec = ix->cfg.precision;
+    const bool bytes = prec == FLINNG_PREC_FP8;
     const uint64_t chunk = kTcChunkRows;
     const uint64_t cap = n < chunk ? n : chunk;     // rows the workspace was sized for
     Carver c(ws, ~size_t(0));
-    __nv_bfloat16 *xs = c.take<__nv_bfloat16>(cap * d * 2);
+    char *xq = c.take<char>(cap * qrow_bytes(prec, d));
     float *xn = c.take<float>(cap);
+    float *xr = c.take<float>(cap);
+    float *xsc = c.take<float>(cap);
     unsigned long long *cnt = c.take<unsigned long long>(8);
     unsigned long long *list1 = c.take<unsigned long long>(cap * P + 1);
     unsigned long long *list2 = c.take<unsigned long long>(cap * P + 1);
     FL_CUDA(cudaMemsetAsync(ix->stats, 0, kStats * sizeof(unsigned long long), st));
     if (n == 0) return FLINNG_OK;
     FL_CUDA(cudaMemsetAsync(buckets, 0, n * L * sizeof(uint32_t), st));
-    const __nv_bfloat16 *w1 = static_cast<const __nv_bfloat16 *>(ix->w_split);
+    const char *wq = static_cast<const char *>(ix->w_split);
     CUtensorMap mw1, mw2;
-    FL_TRY(make_map(&mw1, w1, P, d));
-    FL_TRY(make_map(&mw2, w1 + size_t(P) * d, P, d));
+    FL_TRY(make_map(&mw1, wq, P, d, bytes));
+    if (prec == FLINNG_PREC_BF16X2) FL_TRY(make_map(&mw2, wq + size_t(P) * d * 2, P, d, false));
+    else mw2 = mw1;
     // margin factors (see the header comment), in double then rounded up
     const double u = std::ldexp(1.0, -24), up = std::ldexp(1.0, -22);
     auto g = [](double m, double uu) { return m * uu / (1.0 - m * uu); };
     const double q = (1 + std::ldexp(1.0, -8)) * (1 + std::ldexp(1.0, -8));
-    const double m_blocks = double((d + kTK - 1) / kTK);
-    const double f = (g(kTK, up) + std::ldexp(1.0, -7) * g(2 * kTK, up)) * q +
-                     g(2 * m_blocks, u) * (1 + g(kTK, up)) * (1 + std::ldexp(1.0, -7)) * q +
-                     3.1 * std::ldexp(1.0, -16);
+    const double kb = prec == FLINNG_PREC_FP8 ? 128.0 : double(kTK);     // products per k-block
+    const double m_blocks = std::ceil(double(d) / kb);
+    double f;
+    if (prec == FLINNG_PREC_BF16X2)
+        f = (g(kTK, up) + std::ldexp(1.0, -7) * g(2 * kTK, up)) * q +
+            g(2 * m_blocks, u) * (1 + g(kTK, up)) * (1 + std::ldexp(1.0, -7)) * q + 3.1 * std::ldexp(1.0, -16);
+    else
+        f = g(kb, up) + g(m_blocks, u) * (1 + g(kb, up));    // times (||x|| + ||e_x||)(||w|| + ||e_w||)
     const float c_norm = std::nextafter(float(f * 1.0001), INFINITY);
     const float c_sub = std::nextafter(float(std::sqrt(double(d)) * std::ldexp(1.0, -125)), INFINITY);
     const float tiny = std::nextafter(float(8.0 * d * std::ldexp(1.0, -126)), INFINITY);
     const double g2d = 2.0 * d * std::ldexp(1.0, -24) / (1.0 - 2.0 * d * std::ldexp(1.0, -24));
     const float g2 = std::nextafter(float(2.0 * g2d * g2d + std::ldexp(1.0, -40)), INFINITY);
-    const size_t smem = size_t(kStages) * kStageBytes + 1024 + 256;
-    FL_TRY(ensure_dyn_smem((const void *)k_srp_tc, smem));
     for (uint64_t r0 = 0; r0 < n; r0 += chunk) {
         const uint64_t rows = (n - r0) < chunk ? (n - r0) : chunk;
-        k_split_rows<<<warp_grid(rows), 256, 0, st>>>(x + r0 * ld, ld, rows, d, xs, xs + rows * d, xn);
-        count_launch();
-        FL_CUDA(cudaGetLastError());
+        FL_TRY(quant_rows(prec, x + r0 * ld, ld, rows, d, xq, xn, xr, xsc, st));
         CUtensorMap mx1, mx2;
-        FL_TRY(make_map(&mx1, xs, rows, d));
-        FL_TRY(make_map(&mx2, xs + rows * d, rows, d));
+        FL_TRY(make_map(&mx1, xq, rows, d, bytes));
+        if (prec == FLINNG_PREC_BF16X2) FL_TRY(make_map(&mx2, xq + rows * d * 2, rows, d, false));
+        else mx2 = mx1;
         FL_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), st));
         TcArgs a{};
         a.n = rows;
@@ -577,6 +786,10 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
         a.K = K;
         a.xnorm = xn;
         a.wnorm = ix->w_norm;
+        a.xres = xr;
+        a.wres = ix->w_aux;
+        a.xscale = xsc;
+        a.wscale = ix->w_aux ? ix->w_aux + P : nullptr;
         a.c_norm = c_norm;
         a.c_sub = c_sub;
         a.tiny = tiny;
@@ -585,10 +798,9 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
         a.rlist = list1;
         a.rcount = cnt;
         a.err = ix->tc_err;
-        dim3 grid((P + kTN - 1) / kTN, (unsigned)((rows + kTM - 1) / kTM));
-        k_srp_tc<<<grid, kTcThreads, smem, st>>>(mx1, mx2, mw1, mw2, a);
-        count_launch();
-        FL_CUDA(cudaGetLastError());
+        if (prec == FLINNG_PREC_BF16X2) FL_TRY(launch_tc<kFormBf16x2>(mx1, mx2, mw1, mw2, a, rows, st));
+        else if (prec == FLINNG_PREC_BF16) FL_TRY(launch_tc<kFormBf16>(mx1, mx2, mw1, mw2, a, rows, st));
+        else FL_TRY(launch_tc<kFormFp8>(mx1, mx2, mw1, mw2, a, rows, st));
         // stage 2: compensated fp32; stage 3: fp64 / exact
         k_srp_recheck2<<<152 * 4, 256, 0, st>>>(x + r0 * ld, ld, ix->srp_w, d, L, K, g2, tiny, list1, cnt,
                                                buckets + r0 * L, list2, cnt + 1, ix->stats);

@@ -19,7 +19,7 @@ from . import _build
 
 OK, ERR_INVALID_ARG, ERR_OOM, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT = range(6)
 COSINE_SRP, JACCARD_DOPH = 0, 1
-PREC_FP32, PREC_BF16X2 = 0, 1
+PREC_FP32, PREC_BF16X2, PREC_BF16, PREC_FP8 = 0, 1, 2, 3
 QUERY_PLAIN, QUERY_FUSED, QUERY_GRAPH = 0, 1, 2
 
 
