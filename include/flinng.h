@@ -406,7 +406,9 @@ int flinng_query_noalloc(flinng_index *idx, const flinng_points *q, uint32_t nq,
  * and scratch, so batches overlap on the device; a slot takes the next batch
  * as soon as its previous one completes. An insert runs when every batch in
  * flight on its index has finished, in arrival order with that index's
- * queries (later queries see the inserted points). Results equal those of
+ * queries (later queries see the inserted points), on a host thread of its
+ * own: the other indices keep being served meanwhile, and its own index
+ * takes no batch until the insert is done. Results equal those of
  * flinng_query on the index as it stood when the query ran. */
 typedef struct flinng_server flinng_server;
 

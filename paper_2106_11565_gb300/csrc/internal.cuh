@@ -214,10 +214,12 @@ void destroy_graphs(flinng_index *ix);
 // Decode from caller-given per-cell counts (nq x B*R, each clamped to max_count)
 // instead of gathering them; qbuckets unused then.
 int query_launch_counts(flinng_index *ix, const uint32_t *qbuckets, const uint16_t *counts, uint32_t max_count,
-                        uint32_t nq, const uint32_t *k, uint32_t k_max, uint32_t *out_ids, uint16_t *out_scores);
+                        uint32_t nq, const uint32_t *k, uint32_t k_max, uint32_t *out_ids, uint16_t *out_scores,
+                        const uint32_t *out_row = nullptr);
+// out_row (optional, device): per query, its row of out_ids / out_scores
 int query_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
                  const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
-                 uint16_t *out_scores);
+                 uint16_t *out_scores, const uint32_t *out_row = nullptr);
 int counts_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
                   uint16_t *out_counts);
 

@@ -64,13 +64,14 @@ void pick_buffer(QArgs &a, int NT, const QueryTuning *tune, size_t extra, size_t
 
 int query_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
                  const uint32_t *k, uint32_t k_max, uint32_t *out_ids,
-                 uint16_t *out_scores)
+                 uint16_t *out_scores, const uint32_t *out_row)
 {
-    return query_launch_counts(ix, qbuckets, nullptr, 0, nq, k, k_max, out_ids, out_scores);
+    return query_launch_counts(ix, qbuckets, nullptr, 0, nq, k, k_max, out_ids, out_scores, out_row);
 }
 
 int query_launch_counts(flinng_index *ix, const uint32_t *qbuckets, const uint16_t *counts, uint32_t max_count,
-                        uint32_t nq, const uint32_t *k, uint32_t k_max, uint32_t *out_ids, uint16_t *out_scores)
+                        uint32_t nq, const uint32_t *k, uint32_t k_max, uint32_t *out_ids, uint16_t *out_scores,
+                        const uint32_t *out_row)
 {
     if (nq == 0) return FLINNG_OK;
     QArgs a = make_args(ix, qbuckets, nq);
@@ -85,6 +86,7 @@ int query_launch_counts(flinng_index *ix, const uint32_t *qbuckets, const uint16
     a.k_max = k_max;
     a.out_ids = out_ids;
     a.out_scores = out_scores;
+    a.out_row = out_row;
     // CTA size: when shared memory admits only one or two CTAs per SM (large
     // B*R), wider CTAs keep about 1,024 threads per SM decoding
     int NT = 256;

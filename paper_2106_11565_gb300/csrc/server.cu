@@ -10,7 +10,8 @@
 // earlier ones run. A slot is reused as soon as its batch's event completes;
 // its results are copied back and the requests marked done. An insert runs
 // once every batch in flight on its index has finished, in arrival order
-// with that index's queries (later queries see the new points).
+// with that index's queries (later queries see the new points), on a thread
+// of its own so that the other indices keep being served.
 // Admission is by HBM budget: an index is accepted only if its device
 // memory plus the slots' scratch fits, an insert only if the index has
 // capacity left and stays within the budget.
@@ -20,9 +21,11 @@
 // small descriptor per request; the query kernel then writes each result row
 // straight into the caller's output buffers too. Elsewhere the host copies
 // the inputs into pinned staging first and the results back out of it.
+#include <atomic>
 #include <chrono>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <thread>
 #include <vector>
 
@@ -48,11 +51,23 @@ struct Slot {
     size_t hbytes = 0;
 };
 
+// An insert runs on a thread of its own (flinng_insert on the index's own
+// stream) while the scheduling thread keeps serving the other indices; the
+// index takes no batch until it is done.
+struct InsertJob {
+    std::thread th;
+    std::atomic<bool> finished{false};
+    bool active = false;
+    int rc = FLINNG_OK;
+    uint64_t req = 0;
+};
+
 struct ServerIndex {
     flinng_index *ix;
     uint32_t version = 0;      // inserts applied
     uint32_t inflight = 0;     // batches on the device
     std::deque<uint64_t> pending;
+    std::unique_ptr<InsertJob> job{new InsertJob()};
 };
 
 // Per-slot layout (device and host mirror): counter + stats, the batch
@@ -183,7 +198,7 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs, uin
     uint32_t *hr = reinterpret_cast<uint32_t *>(hh + ho_.row);
     uint64_t *ho = reinterpret_cast<uint64_t *>(hh + ho_.in_off);
     const bool big_srp = srp && uint64_t(ix->P) * ix->cfg.dim > (1ull << 18);
-    slot.direct = srv->device_gather && !big_srp;
+    slot.direct = srv->device_gather;
     FL_CUDA(cudaEventRecord(slot.start, slot.stream));
     ho[0] = 0;
     if (srv->device_gather) {
@@ -243,7 +258,13 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs, uin
         uint32_t *qb = reinterpret_cast<uint32_t *>(d + Lo.qb);
         rc = srp_hash(ix, reinterpret_cast<const float *>(d + Lo.in_el), ix->cfg.dim, nb, qb, nullptr, d + Lo.srp,
                       (2 * size_t(nb) * ix->P + 64) * 8);
-        if (rc == FLINNG_OK) rc = query_launch(ix, qb, nb, dk, km, dids, dsc);
+        if (slot.direct) {
+            dids = out_ids;
+            dsc = out_scores;
+        }
+        if (rc == FLINNG_OK)
+            rc = query_launch(ix, qb, nb, dk, km, dids, dsc,
+                              slot.direct ? reinterpret_cast<const uint32_t *>(dh + ho_.row) : nullptr);
     } else {
         FusedQuery fq{nb, reinterpret_cast<const float *>(d + Lo.in_el), ix->cfg.dim,
                       reinterpret_cast<const uint64_t *>(dh + ho_.in_off), reinterpret_cast<const uint32_t *>(d + Lo.in_el)};
@@ -357,7 +378,7 @@ int flinng_server_add_index(flinng_server *srv, flinng_index *ix, uint32_t *inde
     srv->bytes_used = others + need;
     ServerIndex S;
     S.ix = ix;
-    srv->idx.push_back(S);
+    srv->idx.push_back(std::move(S));
     if (index_id) *index_id = uint32_t(srv->idx.size() - 1);
     return FLINNG_OK;
 }
@@ -393,7 +414,18 @@ int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_
     for (ServerIndex &S : srv->idx) {
         S.pending.clear();
         S.inflight = 0;
+        if (S.job->th.joinable()) S.job->th.join();
+        S.job->active = false;
     }
+    // an early return (a failed launch) still waits for running inserts
+    struct JoinInserts {
+        flinng_server *srv;
+        ~JoinInserts()
+        {
+            for (ServerIndex &S : srv->idx)
+                if (S.job->th.joinable()) S.job->th.join();
+        }
+    } join_inserts{srv};
     if (n) FL_CUDA(cudaEventRecord(srv->ref, srv->slots[0].stream));
     const double t0 = now_s();
     uint64_t next = 0, done = 0, batches = 0;
@@ -442,33 +474,50 @@ int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_
             s.reqs.clear();
             progress = true;
         }
-        // inserts at the head of an idle index
-        for (size_t ii = 0; ii < srv->idx.size(); ++ii) {
-            ServerIndex &S = srv->idx[ii];
-            while (!S.pending.empty() && reqs[S.pending.front()].kind == FLINNG_REQ_INSERT && S.inflight == 0) {
-                const uint64_t r = S.pending.front();
-                S.pending.pop_front();
-                const flinng_request &q = reqs[r];
-                res[r].t_start = now_s() - t0;
-                res[r].version = S.version;
-                int rc;
-                if (S.ix->n_points + q.n > S.ix->cfg.capacity) {
-                    rc = FLINNG_ERR_CAPACITY;
-                } else {
-                    rc = flinng_insert(S.ix, static_cast<const flinng_points *>(q.data), q.n, q.perm,
-                                       (int)q.on_device);
-                    if (rc == FLINNG_OK) {
-                        ++S.version;
-                        uint64_t total = 0;
-                        for (const ServerIndex &T : srv->idx) total += flinng_device_bytes(T.ix);
-                        srv->bytes_used = total + uint64_t(Lo.total) * srv->slots.size();
-                    }
-                }
-                res[r].status = uint32_t(rc);
+        // inserts that finished on their threads
+        for (ServerIndex &S : srv->idx) {
+            InsertJob &J = *S.job;
+            if (!J.active || !J.finished.load(std::memory_order_acquire)) continue;
+            J.th.join();
+            J.active = false;
+            res[J.req].status = uint32_t(J.rc);
+            res[J.req].t_done = now_s() - t0;
+            if (J.rc == FLINNG_OK) {
+                ++S.version;
+                uint64_t total = 0;
+                for (const ServerIndex &T : srv->idx) total += flinng_device_bytes(T.ix);
+                srv->bytes_used = total + uint64_t(Lo.total) * srv->slots.size();
+            }
+            ++done;
+            progress = true;
+        }
+        // an insert at the head of an idle index starts on its own thread
+        for (ServerIndex &S : srv->idx) {
+            InsertJob &J = *S.job;
+            if (J.active || S.pending.empty() || reqs[S.pending.front()].kind != FLINNG_REQ_INSERT || S.inflight)
+                continue;
+            const uint64_t r = S.pending.front();
+            S.pending.pop_front();
+            const flinng_request &q = reqs[r];
+            res[r].t_start = now_s() - t0;
+            res[r].version = S.version;
+            progress = true;
+            if (S.ix->n_points + q.n > S.ix->cfg.capacity) {
+                res[r].status = FLINNG_ERR_CAPACITY;
                 res[r].t_done = now_s() - t0;
                 ++done;
-                progress = true;
+                continue;
             }
+            J.active = true;
+            J.req = r;
+            J.rc = FLINNG_OK;
+            J.finished.store(false, std::memory_order_relaxed);
+            flinng_index *ix = S.ix;
+            InsertJob *jp = &J;
+            J.th = std::thread([ix, jp, &q]() {
+                jp->rc = flinng_insert(ix, static_cast<const flinng_points *>(q.data), q.n, q.perm, (int)q.on_device);
+                jp->finished.store(true, std::memory_order_release);
+            });
         }
         // fill free slots with batches, indices in turn
         for (Slot &s : srv->slots) {
@@ -477,7 +526,7 @@ int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_
             for (size_t tries = 0; tries < srv->idx.size() && !launched; ++tries) {
                 const size_t ii = (rr + tries) % srv->idx.size();
                 ServerIndex &S = srv->idx[ii];
-                if (S.pending.empty() || reqs[S.pending.front()].kind != FLINNG_REQ_QUERY) continue;
+                if (S.job->active || S.pending.empty() || reqs[S.pending.front()].kind != FLINNG_REQ_QUERY) continue;
                 const bool sets = S.ix->cfg.metric != FLINNG_COSINE_SRP;
                 uint64_t elems = 0;
                 s.index = uint32_t(ii);
@@ -505,6 +554,7 @@ int flinng_server_replay(flinng_server *srv, const flinng_request *reqs, uint64_
         if (!progress) {
             bool any_busy = false;
             for (const Slot &s : srv->slots) any_busy |= s.busy;
+            for (const ServerIndex &S : srv->idx) any_busy |= S.job->active;
             if (!any_busy && next < n) {
                 const double wait = reqs[next].arrival_s - (now_s() - t0);
                 if (wait > 200e-6) std::this_thread::sleep_for(std::chrono::duration<double>(wait - 100e-6));
