@@ -354,8 +354,9 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 
 def kernel_source_hash() -> str:
+    """Hash of the query kernels' sources (the kernels and their launchers)."""
     h = hashlib.sha256()
-    for f in ("query.cu", "query_impl.cuh", "query_c16.cu", "internal.cuh"):
+    for f in ("query.cu", "query_impl.cuh", "query_c16.cu"):
         h.update(open(os.path.join(ROOT, "paper_2106_11565_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -853,15 +854,48 @@ def latency_breakdown(req, res, F) -> dict:
             "device": pc(r["d_done"] - r["d_start"]), "harvest": pc(r["t_done"] - r["d_done"])}
 
 
+INSERT_POINTS = 1000   # points of the timed insert batch
+
+
+def time_insert(F, ix, c: dict, dev, flush, reps: int = 1) -> dict | None:
+    """CUDA-event time of inserting INSERT_POINTS further reads (genomic
+    workloads; Alg. 1 over a fresh permutation of the batch) into ix, which
+    must have room for them; the index keeps them afterwards."""
+    import torch
+    if c["metric"] == "cosine" or c.get("url"):
+        return None
+    g = WL.genomic_reads(c["seed"] + 2000, c["ref_len"], INSERT_POINTS * reps, c["read_len"], 1, kmer=c["kmer"])
+    off, el = g["off"], g["elems"]
+    ms = []
+    for r in range(reps):
+        lo, hi = r * INSERT_POINTS, (r + 1) * INSERT_POINTS
+        o = (off[lo:hi + 1] - off[lo]).astype(np.uint64)
+        e = np.ascontiguousarray(el[off[lo]:off[hi]])
+        pts = (torch.from_numpy(o.view(np.int64)).to(dev), torch.from_numpy(e.view(np.int32)).to(dev))
+        perm = torch.from_numpy(WL.group_permutations(c["seed"], c["R"], INSERT_POINTS, batch=11 + r)
+                                .view(np.int32)).to(dev)
+        flush.fill_(r)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ix.insert(pts, perm)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return {"points": INSERT_POINTS, "ms": statistics.mean(ms), "reps": reps,
+            "note": "flinng_insert of further reads from device buffers: hash, Alg. 1 groups, member lists, the new "
+                    "entries sorted per slot and merged into the existing lists, heavy bitmaps"}
+
+
 def configured_point(F, c: dict, dev, d_pts, d_q, flush, steps: int, warmup: int, ex_ids, ex_sims) -> dict:
     """The workload at the parameters its config names: fused form (CUDA
     graph) and plain form throughput, recall@10 (a side key of the line)."""
     import torch
     nq, k = c["nq"], c["k"]
-    ix = F.Index(c["metric"], c["R"], c["B"], c["L"], c["K"], capacity=c["N"], params=c["params"],
-                 dim=c.get("d", 0), W=c["W"])
-    ix.build(d_pts, torch.from_numpy(c["perm"].view(np.int32)).to(dev))
+    ix = F.Index(c["metric"], c["R"], c["B"], c["L"], c["K"], capacity=c["N"] + 3 * INSERT_POINTS,
+                 params=c["params"], dim=c.get("d", 0), W=c["W"])
+    d_perm = torch.from_numpy(c["perm"].view(np.int32)).to(dev)
     stream = torch.cuda.current_stream()
+    build_ms = timed_steps(lambda: ix.build(d_pts, d_perm), flush, stream, 3, 2)
     fp, _, _, keepq = ix._points(d_q)
     qb = torch.empty((nq, c["L"]), dtype=torch.int32, device=dev)
     ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
@@ -887,17 +921,22 @@ def configured_point(F, c: dict, dev, d_pts, d_q, flush, steps: int, warmup: int
                    f"{k} for every query"}
     if ex_ids is not None:
         out["recall"] = recall_scores(c, got[gt_sample(c)], ex_ids, ex_sims)
+    out["build_ms"] = statistics.mean(build_ms)
+    out["insert"] = time_insert(F, ix, c, dev, flush, reps=3)
     ix.close()
     return out
 
 
-def timed_steps(fn, flush, stream, steps: int, warmup: int) -> list:
+def timed_steps(fn, flush, stream, steps: int, warmup: int, nvtx: str | None = None) -> list:
     """CUDA-event times (ms) of ``steps`` calls of fn, L2 flushed before each,
-    after ``warmup`` untimed calls."""
+    after ``warmup`` untimed calls; ``nvtx`` names an NVTX range around the
+    timed calls (profilers select the launches inside it)."""
     import torch
     for it in range(warmup):
         flush.fill_(it)
         fn()
+    if nvtx:
+        torch.cuda.nvtx.range_push(nvtx)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for it in range(steps):
         flush.fill_(it + 1)
@@ -905,6 +944,8 @@ def timed_steps(fn, flush, stream, steps: int, warmup: int) -> list:
         fn()
         ev[it][1].record(stream)
     torch.cuda.synchronize()
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
     return [a.elapsed_time(b) for a, b in ev]
 
 
@@ -935,11 +976,11 @@ def run_headline(args, c: dict, rank: int, world: int) -> dict | None:
     d_pts, d_q = to_dev(ct["pts"]), to_dev(ct["q"])
     d_perm = torch.from_numpy(ct["perm"].view(np.int32)).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)   # > L2 (129 MB)
-    ix = F.Index(ct["metric"], ct["R"], ct["B"], L, ct["K"], capacity=ct["N"], params=ct["params"],
-                 dim=ct.get("d", 0), W=ct["W"])
+    ix = F.Index(ct["metric"], ct["R"], ct["B"], L, ct["K"], capacity=ct["N"] + 3 * INSERT_POINTS,
+                 params=ct["params"], dim=ct.get("d", 0), W=ct["W"])
 
     # ---- build: 2 warm-up builds, then 3 timed (each replaces the index)
-    build_ms = timed_steps(lambda: ix.build(d_pts, d_perm), flush, stream, 3, 2)
+    build_ms = timed_steps(lambda: ix.build(d_pts, d_perm), flush, stream, 3, 2, nvtx="build")
 
     # ---- kernel-only forms on device buffers (k for every query)
     qb = torch.empty((nq, L), dtype=torch.int32, device=dev)
@@ -968,12 +1009,13 @@ def run_headline(args, c: dict, rank: int, world: int) -> dict | None:
     plain()
     torch.cuda.synchronize()
     assert torch.equal(ids, p_ids) and torch.equal(sc, p_sc), "fused form != plain form"
-    fused_ms = timed_steps(fused, flush, stream, args.steps, max(3, args.warmup))
+    fused_ms = timed_steps(fused, flush, stream, args.steps, max(3, args.warmup), nvtx="fused form")
     # plain form with a mid event per step: hash vs count/decode/top-k
     for it in range(max(3, args.warmup)):
         flush.fill_(it)
         plain()
     pev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    torch.cuda.nvtx.range_push("plain form")
     for it in range(args.steps):
         flush.fill_(it + 1)
         pev[it][0].record(stream)
@@ -981,6 +1023,7 @@ def run_headline(args, c: dict, rank: int, world: int) -> dict | None:
         plain()
         pev[it][2].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     mid[:] = []
     plain_ms = [a.elapsed_time(b) for a, _, b in pev]
     hash_ms = [a.elapsed_time(m) for a, m, _ in pev]
@@ -1017,10 +1060,12 @@ def run_headline(args, c: dict, rank: int, world: int) -> dict | None:
     torch.cuda.synchronize()
     launches0 = F.kernel_launches()
     steps = []
+    torch.cuda.nvtx.range_push("serving form")
     for it in range(args.steps):
         ids_s, sc_s, res = srv.replay(traces[it], out=(o_ids, o_sc))
         steps.append(serving_step_stats(traces[it], res, F))
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     launches = F.kernel_launches() - launches0
     t_end = time.time()
     clk = clocks.stop(t_load, t_end)
@@ -1091,6 +1136,7 @@ def run_headline(args, c: dict, rank: int, world: int) -> dict | None:
             "note": "one launch = the fused form over the whole query batch (CUDA graph, L2 flushed); the "
                     "serving form runs the same kernel on batches of its own size"}
     index_bytes = ix.device_bytes
+    insert = time_insert(F, ix, ct, dev, flush, reps=3)        # last: the index keeps the new points
     # same points and queries: the exact neighbours are the same
     configured = configured_point(F, c, dev, d_pts, d_q, flush, max(3, min(args.steps, 10)),
                                   max(3, args.warmup), ex_ids, ex_sims)
@@ -1125,7 +1171,7 @@ def run_headline(args, c: dict, rank: int, world: int) -> dict | None:
                        "arrival to the last result written into the caller's buffer (host clock)"},
         "gpu_launches": int(launches),
         "build": {"ms": statistics.mean(build_ms), "points_per_s": ct["N"] / (statistics.mean(build_ms) / 1e3),
-                  "n_cells": int(ex["off"][-1]), "index_bytes": index_bytes},
+                  "n_cells": int(ex["off"][-1]), "index_bytes": index_bytes, "insert": insert},
         "clocks": clk,
         "at_configured_params": configured,
     }

@@ -13,6 +13,9 @@
 // and new entries in one array; each slot is then sorted and deduplicated (a
 // Bloom-filter bit is set once, Sec. 3.3) and the slots are compacted into
 // the final CSR.
+#include <algorithm>
+#include <utility>
+
 #include "internal.cuh"
 #include "trace.h"
 
@@ -147,34 +150,6 @@ __global__ void k_slot_hist(const uint32_t *__restrict__ buckets, uint64_t n, ui
     }
 }
 
-__global__ void k_slot_add_old(const uint32_t *__restrict__ off, uint64_t nslot,
-                               uint32_t *__restrict__ hist)
-{
-    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nslot;
-         s += uint64_t(gridDim.x) * blockDim.x)
-        hist[s] += off[s + 1] - off[s];
-}
-
-// cursor[s] = toff[s] + old length; old list copied to the head of the slot.
-__global__ void k_slot_copy_old(const uint32_t *__restrict__ off, const uint16_t *__restrict__ cells,
-                                const uint32_t *__restrict__ toff, uint64_t nslot, int have_old,
-                                uint32_t *__restrict__ cursor, uint16_t *__restrict__ tmp)
-{
-    const int lane = threadIdx.x & 31;
-    const uint64_t gw = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-    for (uint64_t s = gw; s < nslot; s += nw) {
-        const uint32_t dst = toff[s];
-        uint32_t len = 0;
-        if (have_old) {
-            const uint32_t beg = off[s];
-            len = off[s + 1] - beg;
-            for (uint32_t t = lane; t < len; t += 32) tmp[dst + t] = cells[beg + t];
-        }
-        if (lane == 0) cursor[s] = dst + len;
-    }
-}
-
 __global__ void k_slot_scatter_new(const uint32_t *__restrict__ buckets, const uint16_t *__restrict__ gid,
                                    uint64_t n_old, uint64_t n, uint32_t L, uint32_t W, uint32_t R,
                                    uint32_t B, uint32_t rp, uint32_t *__restrict__ cursor,
@@ -191,25 +166,69 @@ __global__ void k_slot_scatter_new(const uint32_t *__restrict__ buckets, const u
     }
 }
 
-// Sort and deduplicate each slot in place; ulen[s] = distinct cells.
-// <= 32 entries: warp bitonic sort in registers. More: a bitmap over all
-// B*R cells in shared memory, read back in cell order.
+__device__ __forceinline__ void cex(uint32_t &a, uint32_t &b)
+{
+    const uint32_t lo = min(a, b);
+    b = max(a, b);
+    a = lo;
+}
+
+// Thread per slot: the new cells of a slot holding at most kSmallSlot of them
+// are sorted (Batcher's odd-even merge network for eight inputs, in
+// registers) and deduplicated in place (a Bloom-filter bit is set once,
+// Sec. 3.3); ulen[s] = distinct cells. Larger slots go to a worklist.
+constexpr uint32_t kSmallSlot = 8;
+
+__global__ void k_slot_unique_small(const uint32_t *__restrict__ toff, uint64_t nslot, uint16_t *__restrict__ tmp,
+                                    uint32_t *__restrict__ ulen, uint32_t *__restrict__ big,
+                                    uint32_t *__restrict__ nbig)
+{
+    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nslot;
+         s += uint64_t(gridDim.x) * blockDim.x) {
+        const uint32_t beg = toff[s], len = toff[s + 1] - beg;
+        if (len <= 1) {
+            ulen[s] = len;
+            continue;
+        }
+        if (len > kSmallSlot) {
+            big[atomicAdd(nbig, 1u)] = uint32_t(s);
+            continue;
+        }
+        uint32_t v[8];
+#pragma unroll
+        for (uint32_t i = 0; i < 8; ++i) v[i] = i < len ? uint32_t(tmp[beg + i]) : 0xFFFFFFFFu;
+        cex(v[0], v[1]); cex(v[2], v[3]); cex(v[4], v[5]); cex(v[6], v[7]);
+        cex(v[0], v[2]); cex(v[1], v[3]); cex(v[4], v[6]); cex(v[5], v[7]);
+        cex(v[1], v[2]); cex(v[5], v[6]);
+        cex(v[0], v[4]); cex(v[1], v[5]); cex(v[2], v[6]); cex(v[3], v[7]);
+        cex(v[2], v[4]); cex(v[3], v[5]);
+        cex(v[1], v[2]); cex(v[3], v[4]); cex(v[5], v[6]);
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const bool keep = v[i] != 0xFFFFFFFFu && (i == 0 || v[i] != v[i > 0 ? i - 1 : 0]);
+            if (keep) tmp[beg + cnt++] = uint16_t(v[i]);
+        }
+        ulen[s] = cnt;
+    }
+}
+
+// Warp per worklist slot: sort and deduplicate in place. <= 32 cells: warp
+// bitonic sort in registers; more: a bitmap over the B*R cells in shared
+// memory, read back in cell order.
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_slot_unique(const uint32_t *__restrict__ toff, uint64_t nslot, uint32_t BR,
-              uint16_t *__restrict__ tmp, uint32_t *__restrict__ ulen)
+k_slot_unique_big(const uint32_t *__restrict__ toff, const uint32_t *__restrict__ big,
+                  const uint32_t *__restrict__ nbig, uint32_t BR, uint16_t *__restrict__ tmp,
+                  uint32_t *__restrict__ ulen)
 {
     extern __shared__ uint32_t bm_all[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t nwords = (BR + 31) / 32;
     uint32_t *bm = bm_all + warp * nwords;
-    const uint64_t gw = uint64_t(blockIdx.x) * kWarpsPerBlock + warp;
-    const uint64_t nw = uint64_t(gridDim.x) * kWarpsPerBlock;
-    for (uint64_t s = gw; s < nslot; s += nw) {
+    const uint32_t nb = *nbig;
+    for (uint32_t i = blockIdx.x * kWarpsPerBlock + warp; i < nb; i += gridDim.x * kWarpsPerBlock) {
+        const uint32_t s = big[i];
         const uint32_t beg = toff[s], len = toff[s + 1] - beg;
-        if (len == 0) {
-            if (lane == 0) ulen[s] = 0;
-            continue;
-        }
         if (len <= 32) {
             uint32_t v = lane < len ? uint32_t(tmp[beg + lane]) : 0xFFFFFFFFu;
 #pragma unroll
@@ -262,16 +281,134 @@ k_slot_unique(const uint32_t *__restrict__ toff, uint64_t nslot, uint32_t BR,
     }
 }
 
-__global__ void k_slot_compact(const uint32_t *__restrict__ toff, const uint32_t *__restrict__ off,
-                               uint64_t nslot, const uint16_t *__restrict__ tmp,
-                               uint16_t *__restrict__ cells)
+// Merge of each slot's old list (sorted, distinct) with its new cells (sorted,
+// distinct, from k_slot_unique_*). A slot whose two lists together hold at
+// most kThreadMerge cells is handled by one thread (two-pointer merge);
+// larger ones go to a worklist for a warp. off == nullptr: no old lists.
+constexpr uint32_t kThreadMerge = 64;
+
+__global__ void k_merge_count(const uint32_t *__restrict__ off, const uint16_t *__restrict__ cells,
+                              const uint32_t *__restrict__ dtoff, const uint32_t *__restrict__ dlen,
+                              const uint16_t *__restrict__ dbuf, uint64_t nslot, uint32_t *__restrict__ mlen,
+                              uint32_t *__restrict__ big, uint32_t *__restrict__ nbig)
 {
-    const int lane = threadIdx.x & 31;
-    const uint64_t gw = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-    for (uint64_t s = gw; s < nslot; s += nw) {
-        const uint32_t src = toff[s], dst = off[s], len = off[s + 1] - dst;
-        for (uint32_t t = lane; t < len; t += 32) cells[dst + t] = tmp[src + t];
+    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nslot;
+         s += uint64_t(gridDim.x) * blockDim.x) {
+        const uint32_t oa = off ? off[s] : 0u, na = off ? off[s + 1] - oa : 0u;
+        const uint32_t db = dtoff[s], nb = dlen[s];
+        if (na + nb > kThreadMerge) big[atomicAdd(nbig, 1u)] = uint32_t(s);
+        if (na == 0 || nb == 0) {
+            mlen[s] = na + nb;
+            continue;
+        }
+        if (na + nb > kThreadMerge) continue;           // counted by the warp kernel
+        uint32_t i = 0, j = 0, cnt = 0;
+        uint32_t a = cells[oa], b = dbuf[db];
+        while (i < na && j < nb) {
+            ++cnt;
+            if (a <= b) {
+                if (a == b) {
+                    ++j;
+                    b = j < nb ? dbuf[db + j] : 0u;
+                }
+                ++i;
+                a = i < na ? cells[oa + i] : 0u;
+            } else {
+                ++j;
+                b = j < nb ? dbuf[db + j] : 0u;
+            }
+        }
+        mlen[s] = cnt + (na - i) + (nb - j);
+    }
+}
+
+// Thread per slot (at most kThreadMerge cells in its two lists): the merged,
+// distinct, sorted list written at noff[s].
+__global__ void k_merge_write(const uint32_t *__restrict__ off, const uint16_t *__restrict__ cells,
+                              const uint32_t *__restrict__ dtoff, const uint32_t *__restrict__ dlen,
+                              const uint16_t *__restrict__ dbuf, uint64_t nslot, const uint32_t *__restrict__ noff,
+                              uint16_t *__restrict__ out)
+{
+    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nslot;
+         s += uint64_t(gridDim.x) * blockDim.x) {
+        const uint32_t oa = off ? off[s] : 0u, na = off ? off[s + 1] - oa : 0u;
+        const uint32_t db = dtoff[s], nb = dlen[s];
+        if (na + nb == 0 || na + nb > kThreadMerge) continue;
+        uint32_t dst = noff[s];
+        uint32_t i = 0, j = 0;
+        while (i < na || j < nb) {
+            const uint32_t a = i < na ? uint32_t(cells[oa + i]) : 0xFFFFFFFFu;
+            const uint32_t b = j < nb ? uint32_t(dbuf[db + j]) : 0xFFFFFFFFu;
+            const uint32_t m = min(a, b);
+            i += (a == m) ? 1u : 0u;
+            j += (b == m) ? 1u : 0u;
+            out[dst++] = uint16_t(m);
+        }
+    }
+}
+
+// Warp per worklist slot: one list empty -> a coalesced copy of the other;
+// else the union through a bitmap over the B*R cells in shared memory
+// (count pass: mlen; write pass: the cells in order at noff[s]).
+template <bool WRITE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_merge_big(const uint32_t *__restrict__ off, const uint16_t *__restrict__ cells, const uint32_t *__restrict__ dtoff,
+            const uint32_t *__restrict__ dlen, const uint16_t *__restrict__ dbuf, const uint32_t *__restrict__ big,
+            const uint32_t *__restrict__ nbig, uint32_t BR, uint32_t *__restrict__ mlen,
+            const uint32_t *__restrict__ noff, uint16_t *__restrict__ out)
+{
+    extern __shared__ uint32_t bm_all[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nwords = (BR + 31) / 32;
+    uint32_t *bm = bm_all + warp * nwords;
+    const uint32_t nbg = *nbig;
+    for (uint32_t i = blockIdx.x * kWarpsPerBlock + warp; i < nbg; i += gridDim.x * kWarpsPerBlock) {
+        const uint32_t s = big[i];
+        const uint32_t oa = off ? off[s] : 0u, na = off ? off[s + 1] - oa : 0u;
+        const uint32_t db = dtoff[s], nb = dlen[s];
+        if (na == 0 || nb == 0) {
+            if (WRITE) {
+                const uint16_t *src = na ? cells + oa : dbuf + db;
+                const uint32_t len = na + nb, dst = noff[s];
+                for (uint32_t t = lane; t < len; t += 32) out[dst + t] = src[t];
+            }
+            continue;
+        }
+        for (uint32_t w = lane; w < nwords; w += 32) bm[w] = 0u;
+        __syncwarp();
+        for (uint32_t t = lane; t < na; t += 32) {
+            const uint32_t c = cells[oa + t];
+            atomicOr(&bm[c >> 5], 1u << (c & 31));
+        }
+        for (uint32_t t = lane; t < nb; t += 32) {
+            const uint32_t c = dbuf[db + t];
+            atomicOr(&bm[c >> 5], 1u << (c & 31));
+        }
+        __syncwarp();
+        uint32_t written = 0;
+        const uint32_t dst = WRITE ? noff[s] : 0u;
+        for (uint32_t w0 = 0; w0 < nwords; w0 += 32) {
+            const uint32_t w = w0 + lane;
+            uint32_t bits = w < nwords ? bm[w] : 0u;
+            const uint32_t cnt = __popc(bits);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            if (WRITE) {
+                uint32_t pos = dst + written + incl - cnt;
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    out[pos++] = uint16_t(w * 32 + b);
+                }
+            }
+            written += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (!WRITE && lane == 0) mlen[s] = written;
+        __syncwarp();
     }
 }
 
@@ -284,20 +421,29 @@ __global__ void k_heavy_flag(const uint32_t *__restrict__ off, uint64_t nslot, u
 }
 
 // hidx[s] = bitmap index of heavy slot s (exclusive prefix of the flags) or
-// kEmpty32; each heavy slot's bitmap is written by one warp.
+// kEmpty32; the heavy slots, in slot order, into list.
+__global__ void k_heavy_list(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pre, uint64_t nslot,
+                             uint32_t *__restrict__ hidx, uint32_t *__restrict__ list)
+{
+    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nslot;
+         s += uint64_t(gridDim.x) * blockDim.x) {
+        const bool heavy = flag[s] != 0u;
+        hidx[s] = heavy ? pre[s] : kEmpty32;
+        if (heavy) list[pre[s]] = uint32_t(s);
+    }
+}
+
+// Warp per heavy slot: its cell bitmap.
 __global__ void k_heavy_fill(const uint32_t *__restrict__ off, const uint16_t *__restrict__ cells,
-                             const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pre,
-                             uint64_t nslot, uint32_t BRw, uint32_t *__restrict__ hidx,
+                             const uint32_t *__restrict__ list, uint32_t nh, uint32_t BRw,
                              uint32_t *__restrict__ hbm)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t gw = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-    for (uint64_t s = gw; s < nslot; s += nw) {
-        const bool heavy = flag[s] != 0u;
-        if (lane == 0) hidx[s] = heavy ? pre[s] : kEmpty32;
-        if (!heavy) continue;
-        uint32_t *bm = hbm + uint64_t(pre[s]) * BRw;
+    for (uint64_t i = gw; i < nh; i += nw) {
+        const uint32_t s = list[i];
+        uint32_t *bm = hbm + i * BRw;
         for (uint32_t w = lane; w < BRw; w += 32) bm[w] = 0u;
         __syncwarp();
         const uint32_t beg = off[s], end = off[s + 1];
@@ -312,8 +458,9 @@ __global__ void k_heavy_fill(const uint32_t *__restrict__ off, const uint16_t *_
 }  // namespace
 
 // Cell bitmaps of the heavy slots (those whose list has >= heavy_min cells).
-// Uses the build scratch slot_a / slot_b; grows the bitmap array if needed.
-int build_heavy(flinng_index *ix, void *scan_ws)
+// Uses the build scratch slot_a / slot_b and a worklist of at least
+// n_cells / heavy_min + 1 entries; grows the bitmap array if needed.
+int build_heavy(flinng_index *ix, void *scan_ws, uint32_t *list)
 {
     const cudaStream_t st = ix->stream;
     const uint64_t nslot = ix->nslot;
@@ -321,6 +468,9 @@ int build_heavy(flinng_index *ix, void *scan_ws)
     count_launch();
     FL_CUDA(cudaGetLastError());
     FL_TRY(scan_exclusive(ix->slot_a, ix->slot_b, nslot, scan_ws, st));
+    k_heavy_list<<<thread_blocks(nslot), 256, 0, st>>>(ix->slot_a, ix->slot_b, nslot, ix->hidx, list);
+    count_launch();
+    FL_CUDA(cudaGetLastError());
     FL_CUDA(cudaMemcpyAsync(ix->h_flag, ix->slot_b + nslot, 4, cudaMemcpyDeviceToHost, st));
     FL_CUDA(cudaStreamSynchronize(st));
     const uint32_t nh = *ix->h_flag;
@@ -341,10 +491,12 @@ int build_heavy(flinng_index *ix, void *scan_ws)
     }
     if (nh > 0 && (!ix->hbm || ix->hbm_words < words))
         return set_error(FLINNG_ERR_OOM, "internal: no storage for %u cell bitmaps", nh);
-    k_heavy_fill<<<warp_blocks(nslot), kWarpsPerBlock * 32, 0, st>>>(ix->off, ix->cells, ix->slot_a, ix->slot_b,
-                                                                    nslot, ix->BRw, ix->hidx, ix->hbm);
-    count_launch();
-    FL_CUDA(cudaGetLastError());
+    if (nh > 0) {
+        k_heavy_fill<<<warp_blocks(nh), kWarpsPerBlock * 32, 0, st>>>(ix->off, ix->cells, list, nh, ix->BRw,
+                                                                     ix->hbm);
+        count_launch();
+        FL_CUDA(cudaGetLastError());
+    }
     ix->n_heavy = nh;
     return FLINNG_OK;
 }
@@ -373,11 +525,31 @@ int check_perm(flinng_index *ix, const uint32_t *perm, uint64_t n, void *ws)
     return FLINNG_OK;
 }
 
-size_t insert_workspace_bytes(const flinng_index *ix)
+namespace {
+
+// Entries of the one worklist the reverse-index stage uses in turn: slots of
+// more than kSmallSlot new cells, slots whose merge holds more than
+// kThreadMerge cells, heavy slots.
+uint64_t worklist_entries(const flinng_index *ix, uint64_t n, bool reset)
+{
+    const uint64_t D = n * ix->cfg.L * ix->cfg.R;
+    const uint64_t old = reset ? 0 : ix->n_cells;
+    uint64_t w = D / (kSmallSlot + 1);
+    w = std::max<uint64_t>(w, (old + D) / (kThreadMerge + 1));
+    w = std::max<uint64_t>(w, (old + D) / ix->heavy_min);
+    return std::min<uint64_t>(w, ix->nslot) + 2;
+}
+
+}  // namespace
+
+size_t insert_workspace_bytes(const flinng_index *ix, uint64_t n, bool reset)
 {
     const size_t ns = ix->nslot + 1;
     const size_t big = ns > size_t(ix->BR) + 1 ? ns : size_t(ix->BR) + 1;
-    return carve_bytes<uint32_t>(ns) + carve_bytes<uint32_t>(ix->BR + 1) + scan_workspace_bytes(big);
+    const uint64_t D = n * ix->cfg.L * ix->cfg.R;
+    return 2 * carve_bytes<uint32_t>(ns) + carve_bytes<uint32_t>(ix->BR + 1) +
+           carve_bytes<uint32_t>(worklist_entries(ix, n, reset)) + carve_bytes<uint32_t>(4) +
+           (reset ? 0 : carve_bytes<uint16_t>(D)) + scan_workspace_bytes(big);
 }
 
 int check_groups(flinng_index *ix, const uint16_t *groups, uint64_t n)
@@ -402,9 +574,17 @@ int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *per
     const uint32_t R = ix->cfg.R, B = ix->cfg.B, L = ix->cfg.L, W = ix->cfg.range_bits;
     const uint32_t BR = ix->BR, rp = ix->rp;
     const uint64_t n_old = ix->n_points, N = n_old + n, nslot = ix->nslot;
+    const bool have_old = ix->n_cells > 0;
+    const uint64_t D = n * L * R;   // new (table, cell) entries before deduplication
     Carver c(ws, ~size_t(0));
-    uint32_t *cursor = c.take<uint32_t>(nslot + 1);
+    uint32_t *dtoff = c.take<uint32_t>(nslot + 1);     // new entries of slot s start here
+    uint32_t *cursor = c.take<uint32_t>(nslot + 1);    // scatter cursors, then merged lengths
     uint32_t *mcur = c.take<uint32_t>(BR + 1);
+    uint32_t *work = c.take<uint32_t>(worklist_entries(ix, n, !have_old));
+    uint32_t *cnt = c.take<uint32_t>(4);
+    // the new entries: in the build scratch for a build from scratch, in the
+    // workspace for an insert (the scratch then receives the merged lists)
+    uint16_t *dbuf = have_old ? c.take<uint16_t>(D) : ix->cells_tmp;
     void *scan_ws = c.base + ((c.used + 255) & ~size_t(255));
 
     // groups of the new points: Alg. 1 from the permutations, or given outright
@@ -437,50 +617,69 @@ int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *per
 
     stage1.end();
     TraceRange stage2("reverse index");
-    // reverse index: histogram of old lists + new entries per slot
-    uint32_t *hist = ix->slot_a, *toff = ix->slot_b;
-    const int have_old = (n_old > 0 && ix->n_cells > 0) ? 1 : 0;
+    // 1. the new entries by slot: counting sort (histogram, scan, scatter)
+    uint32_t *hist = ix->slot_a;
     FL_CUDA(cudaMemsetAsync(hist, 0, (nslot + 1) * sizeof(uint32_t), st));
+    FL_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(uint32_t), st));
     if (n > 0) {
         k_slot_hist<<<thread_blocks(n * L), 256, 0, st>>>(buckets, n, L, W, R, hist);
         count_launch();
         FL_CUDA(cudaGetLastError());
     }
-    if (have_old) {
-        k_slot_add_old<<<thread_blocks(nslot), 256, 0, st>>>(ix->off, nslot, hist);
-        count_launch();
-        FL_CUDA(cudaGetLastError());
-    }
-    FL_TRY(scan_exclusive(hist, toff, nslot, scan_ws, st));
-    k_slot_copy_old<<<warp_blocks(nslot), kWarpsPerBlock * 32, 0, st>>>(
-        ix->off, ix->cells, toff, nslot, have_old, cursor, ix->cells_tmp);
-    count_launch();
-    FL_CUDA(cudaGetLastError());
+    FL_TRY(scan_exclusive(hist, dtoff, nslot, scan_ws, st));
     if (n > 0) {
-        k_slot_scatter_new<<<thread_blocks(n * L), 256, 0, st>>>(buckets, ix->gid, n_old, n, L, W, R, B,
-                                                                 rp, cursor, ix->cells_tmp);
+        FL_CUDA(cudaMemcpyAsync(cursor, dtoff, nslot * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+        k_slot_scatter_new<<<thread_blocks(n * L), 256, 0, st>>>(buckets, ix->gid, n_old, n, L, W, R, B, rp, cursor,
+                                                                 dbuf);
         count_launch();
         FL_CUDA(cudaGetLastError());
     }
-    // sort + dedupe each slot; ulen reuses the histogram buffer
-    uint32_t *ulen = hist;
+    // 2. each slot's new cells sorted and deduplicated (dlen reuses the histogram)
+    uint32_t *dlen = hist;
     const size_t smem = size_t(kWarpsPerBlock) * ((BR + 31) / 32) * sizeof(uint32_t);
-    FL_TRY(ensure_dyn_smem((const void *)k_slot_unique, smem));
-    k_slot_unique<<<warp_blocks(nslot), kWarpsPerBlock * 32, smem, st>>>(toff, nslot, BR, ix->cells_tmp, ulen);
+    k_slot_unique_small<<<thread_blocks(nslot), 256, 0, st>>>(dtoff, nslot, dbuf, dlen, work, cnt + 0);
     count_launch();
     FL_CUDA(cudaGetLastError());
-    FL_TRY(scan_exclusive(ulen, ix->off, nslot, scan_ws, st));
-    k_slot_compact<<<warp_blocks(nslot), kWarpsPerBlock * 32, 0, st>>>(toff, ix->off, nslot,
-                                                                       ix->cells_tmp, ix->cells);
+    FL_TRY(ensure_dyn_smem((const void *)k_slot_unique_big, smem));
+    k_slot_unique_big<<<152 * 8, kWarpsPerBlock * 32, smem, st>>>(dtoff, work, cnt + 0, BR, dbuf, dlen);
     count_launch();
     FL_CUDA(cudaGetLastError());
+    // 3. merged lengths |old u new| (cursor now holds them), new offsets by a scan
+    const uint32_t *old_off = have_old ? ix->off : nullptr;
+    uint32_t *mlen = cursor;
+    k_merge_count<<<thread_blocks(nslot), 256, 0, st>>>(old_off, ix->cells, dtoff, dlen, dbuf, nslot, mlen, work,
+                                                        cnt + 1);
+    count_launch();
+    FL_CUDA(cudaGetLastError());
+    FL_TRY(ensure_dyn_smem((const void *)k_merge_big<false>, smem));
+    FL_TRY(ensure_dyn_smem((const void *)k_merge_big<true>, smem));
+    if (have_old) {
+        k_merge_big<false><<<152 * 8, kWarpsPerBlock * 32, smem, st>>>(old_off, ix->cells, dtoff, dlen, dbuf, work,
+                                                                       cnt + 1, BR, mlen, nullptr, nullptr);
+        count_launch();
+        FL_CUDA(cudaGetLastError());
+    }
+    uint32_t *noff = ix->slot_b;
+    FL_TRY(scan_exclusive(mlen, noff, nslot, scan_ws, st));
+    // 4. the merged lists written once, in slot order (an insert writes the
+    //    build scratch, then the scratch and the list array trade places)
+    uint16_t *out = have_old ? ix->cells_tmp : ix->cells;
+    k_merge_write<<<thread_blocks(nslot), 256, 0, st>>>(old_off, ix->cells, dtoff, dlen, dbuf, nslot, noff, out);
+    count_launch();
+    FL_CUDA(cudaGetLastError());
+    k_merge_big<true><<<152 * 8, kWarpsPerBlock * 32, smem, st>>>(old_off, ix->cells, dtoff, dlen, dbuf, work,
+                                                                  cnt + 1, BR, nullptr, noff, out);
+    count_launch();
+    FL_CUDA(cudaGetLastError());
+    std::swap(ix->off, ix->slot_b);
+    if (have_old) std::swap(ix->cells, ix->cells_tmp);
     FL_CUDA(cudaMemcpyAsync(ix->h_flag, ix->off + nslot, 4, cudaMemcpyDeviceToHost, st));
     FL_CUDA(cudaStreamSynchronize(st));
     ix->n_cells = *ix->h_flag;
     ix->n_points = N;
     stage2.end();
     TraceRange stage3("heavy bitmaps");
-    FL_TRY(build_heavy(ix, scan_ws));
+    FL_TRY(build_heavy(ix, scan_ws, work));
     return FLINNG_OK;
 }
 

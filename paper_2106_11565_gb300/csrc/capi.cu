@@ -290,7 +290,7 @@ int insert_common(flinng_index *ix, const flinng_points *pts, uint64_t n, const 
     const size_t need = (given_buckets ? 0 : stage_bytes(ix, pts, n, on_device)) + carve_bytes<uint32_t>(uint64_t(R) * n) +
                         carve_bytes<uint16_t>(uint64_t(R) * n) +
                         carve_bytes<uint32_t>(n * L) + perm_check_workspace_bytes(R, n) +
-                        hash_ws_bytes(ix, n) + insert_workspace_bytes(ix) + 4096;
+                        hash_ws_bytes(ix, n) + insert_workspace_bytes(ix, n, reset) + 4096;
     FL_TRY(ws_reserve(ix, need));
     Carver c(ix->ws.ptr, ix->ws.bytes);
     Staged s;
@@ -314,7 +314,7 @@ int insert_common(flinng_index *ix, const flinng_points *pts, uint64_t n, const 
     else FL_TRY(check_perm(ix, dperm, n, pws));
     const size_t hb = hash_ws_bytes(ix, n);
     void *hws = c.take<char>(hb);
-    void *iws = c.take<char>(insert_workspace_bytes(ix));
+    void *iws = c.take<char>(insert_workspace_bytes(ix, n, reset));
     if (given_buckets) {
         if (on_device) {
             FL_CUDA(cudaMemcpyAsync(buckets, given_buckets, n * L * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));

@@ -97,13 +97,13 @@ def test_clock_record_reasons_and_window():
 
 
 def test_recorded_traffic_needs_the_same_kernel_source(monkeypatch):
-    path = os.path.join(ROOT, "profiles", "k_query_fused_C2_traffic.txt")
+    path = os.path.join(ROOT, "profiles", "k_query_fused_C2_R3B4096L512K1_traffic.txt")
     rec = dict(line.split(":", 1) for line in open(path) if ":" in line and not line.startswith("#"))
     h = rec["source_sha256_16"].strip()
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
-    assert bench.recorded_traffic("C2") == float(rec["dram_bytes_per_launch"])
+    assert bench.recorded_traffic("C2_R3B4096L512K1") == float(rec["dram_bytes_per_launch"])
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
-    assert bench.recorded_traffic("C2") is None
+    assert bench.recorded_traffic("C2_R3B4096L512K1") is None
     assert bench.recorded_traffic("C9") is None
 
 

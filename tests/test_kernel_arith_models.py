@@ -265,3 +265,41 @@ def test_radix_select_keeps_exactly_the_k_smallest(seed):
         prefix, mask = block_select(keys, kk, top_shift)
         kept = sorted(v for v in keys if (v & mask) <= prefix)
         assert kept == sorted(keys)[:kk], kk
+
+
+# ---------------------------------------------------------------- build: small-slot sort
+#
+# The build sorts and deduplicates each slot of at most eight cells in one
+# thread's registers with a fixed compare-exchange network (Batcher's odd-even
+# merge sort for eight inputs, nineteen comparators), padded with 0xFFFFFFFF.
+# By the 0-1 principle a network that sorts all 2^8 binary inputs sorts every
+# input; the dedupe then keeps the first of each run.
+
+NET8 = [(0, 1), (2, 3), (4, 5), (6, 7), (0, 2), (1, 3), (4, 6), (5, 7), (1, 2), (5, 6),
+        (0, 4), (1, 5), (2, 6), (3, 7), (2, 4), (3, 5), (1, 2), (3, 4), (5, 6)]
+
+
+def net8_sort(vals):
+    v = list(vals) + [M32] * (8 - len(vals))
+    for i, j in NET8:
+        if v[i] > v[j]:
+            v[i], v[j] = v[j], v[i]
+    return v
+
+
+def test_sort_network_8_sorts_every_binary_input():
+    assert len(NET8) == 19
+    for m in range(256):
+        bits = [(m >> i) & 1 for i in range(8)]
+        assert net8_sort(bits) == sorted(bits)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_small_slot_sort_and_dedupe(seed):
+    rng = np.random.default_rng(900 + seed)
+    for _ in range(200):
+        n = int(rng.integers(0, 9))
+        vals = rng.integers(0, int(rng.choice([3, 20, 65536])), size=n).tolist()
+        v = net8_sort(vals)
+        out = [x for i, x in enumerate(v) if x != M32 and (i == 0 or x != v[i - 1])]
+        assert out == sorted(set(vals))
