@@ -139,14 +139,18 @@ __global__ void k_member_records(const uint32_t *__restrict__ mem, const uint16_
     }
 }
 
+// The (point, table) entries are taken table-major (t = l n + x): the threads
+// in flight then touch the slots and lists of a few tables at a time, which
+// stay in L2, instead of random slots of the whole index.
 __global__ void k_slot_hist(const uint32_t *__restrict__ buckets, uint64_t n, uint32_t L,
                             uint32_t W, uint32_t R, uint32_t *__restrict__ hist)
 {
     const uint64_t total = n * L;
     for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
          t += uint64_t(gridDim.x) * blockDim.x) {
-        const uint32_t l = uint32_t(t % L);
-        atomicAdd(&hist[(uint64_t(l) << W) | buckets[t]], R);
+        const uint32_t l = uint32_t(t / n);
+        const uint64_t x = t % n;
+        atomicAdd(&hist[(uint64_t(l) << W) | buckets[x * L + l]], R);
     }
 }
 
@@ -158,9 +162,9 @@ __global__ void k_slot_scatter_new(const uint32_t *__restrict__ buckets, const u
     const uint64_t total = n * L;
     for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
          t += uint64_t(gridDim.x) * blockDim.x) {
-        const uint64_t x = t / L;
-        const uint32_t l = uint32_t(t % L);
-        const uint32_t pos = atomicAdd(&cursor[(uint64_t(l) << W) | buckets[t]], R);
+        const uint32_t l = uint32_t(t / n);               // table-major, as k_slot_hist
+        const uint64_t x = t % n;
+        const uint32_t pos = atomicAdd(&cursor[(uint64_t(l) << W) | buckets[x * L + l]], R);
         const uint16_t *g = gid + (n_old + x) * rp;
         for (uint32_t r = 0; r < R; ++r) tmp[pos + r] = uint16_t(r * B + g[r]);
     }
@@ -173,39 +177,69 @@ __device__ __forceinline__ void cex(uint32_t &a, uint32_t &b)
     a = lo;
 }
 
+// Append value to list for every lane that wants to, one atomic per warp.
+// All 32 lanes must call it together.
+__device__ __forceinline__ void warp_append(bool want, uint32_t value, uint32_t *__restrict__ list,
+                                            uint32_t *__restrict__ count)
+{
+    const uint32_t m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == lead) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, lead);
+    if (want) list[base + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
 // Thread per slot: the new cells of a slot holding at most kSmallSlot of them
-// are sorted (Batcher's odd-even merge network for eight inputs, in
-// registers) and deduplicated in place (a Bloom-filter bit is set once,
-// Sec. 3.3); ulen[s] = distinct cells. Larger slots go to a worklist.
-constexpr uint32_t kSmallSlot = 8;
+// are sorted in registers by Batcher's odd-even merge network for sixteen
+// inputs (its first nineteen comparators alone sort the first eight, which
+// is all a slot of up to eight cells needs) and deduplicated in place (a
+// Bloom-filter bit is set once, Sec. 3.3); ulen[s] = distinct cells. Larger
+// slots go to a worklist. The loop runs warp-uniformly (the worklist append
+// is warp-aggregated), so lanes past nslot idle in the last round.
+constexpr uint32_t kSmallSlot = 16;
 
 __global__ void k_slot_unique_small(const uint32_t *__restrict__ toff, uint64_t nslot, uint16_t *__restrict__ tmp,
                                     uint32_t *__restrict__ ulen, uint32_t *__restrict__ big,
                                     uint32_t *__restrict__ nbig)
 {
-    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nslot;
-         s += uint64_t(gridDim.x) * blockDim.x) {
-        const uint32_t beg = toff[s], len = toff[s + 1] - beg;
+    // kNet16: (i, j) compare-exchanges
+    constexpr unsigned char kNet16[63][2] = {
+        {0, 1}, {2, 3}, {0, 2}, {1, 3}, {1, 2}, {4, 5}, {6, 7}, {4, 6}, {5, 7}, {5, 6}, {0, 4}, {2, 6},
+        {2, 4}, {1, 5}, {3, 7}, {3, 5}, {1, 2}, {3, 4}, {5, 6}, {8, 9}, {10, 11}, {8, 10}, {9, 11},
+        {9, 10}, {12, 13}, {14, 15}, {12, 14}, {13, 15}, {13, 14}, {8, 12}, {10, 14}, {10, 12}, {9, 13},
+        {11, 15}, {11, 13}, {9, 10}, {11, 12}, {13, 14}, {0, 8}, {4, 12}, {4, 8}, {2, 10}, {6, 14},
+        {6, 10}, {2, 4}, {6, 8}, {10, 12}, {1, 9}, {5, 13}, {5, 9}, {3, 11}, {7, 15}, {7, 11}, {3, 5},
+        {7, 9}, {11, 13}, {1, 2}, {3, 4}, {5, 6}, {7, 8}, {9, 10}, {11, 12}, {13, 14}};
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s - lane < nslot; s += stride) {
+        const bool valid = s < nslot;
+        uint32_t beg = 0, len = 0;
+        if (valid) {
+            beg = toff[s];
+            len = toff[s + 1] - beg;
+        }
+        warp_append(len > kSmallSlot, uint32_t(s), big, nbig);
+        if (!valid || len > kSmallSlot) continue;
         if (len <= 1) {
             ulen[s] = len;
             continue;
         }
-        if (len > kSmallSlot) {
-            big[atomicAdd(nbig, 1u)] = uint32_t(s);
-            continue;
-        }
-        uint32_t v[8];
+        uint32_t v[16];
 #pragma unroll
-        for (uint32_t i = 0; i < 8; ++i) v[i] = i < len ? uint32_t(tmp[beg + i]) : 0xFFFFFFFFu;
-        cex(v[0], v[1]); cex(v[2], v[3]); cex(v[4], v[5]); cex(v[6], v[7]);
-        cex(v[0], v[2]); cex(v[1], v[3]); cex(v[4], v[6]); cex(v[5], v[7]);
-        cex(v[1], v[2]); cex(v[5], v[6]);
-        cex(v[0], v[4]); cex(v[1], v[5]); cex(v[2], v[6]); cex(v[3], v[7]);
-        cex(v[2], v[4]); cex(v[3], v[5]);
-        cex(v[1], v[2]); cex(v[3], v[4]); cex(v[5], v[6]);
+        for (uint32_t i = 0; i < 16; ++i) v[i] = i < len ? uint32_t(tmp[beg + i]) : 0xFFFFFFFFu;
+        if (len <= 8) {
+#pragma unroll
+            for (int c = 0; c < 19; ++c) cex(v[kNet16[c][0]], v[kNet16[c][1]]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 63; ++c) cex(v[kNet16[c][0]], v[kNet16[c][1]]);
+        }
         uint32_t cnt = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < 16; ++i) {
             const bool keep = v[i] != 0xFFFFFFFFu && (i == 0 || v[i] != v[i > 0 ? i - 1 : 0]);
             if (keep) tmp[beg + cnt++] = uint16_t(v[i]);
         }
@@ -292,11 +326,19 @@ __global__ void k_merge_count(const uint32_t *__restrict__ off, const uint16_t *
                               const uint16_t *__restrict__ dbuf, uint64_t nslot, uint32_t *__restrict__ mlen,
                               uint32_t *__restrict__ big, uint32_t *__restrict__ nbig)
 {
-    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nslot;
-         s += uint64_t(gridDim.x) * blockDim.x) {
-        const uint32_t oa = off ? off[s] : 0u, na = off ? off[s + 1] - oa : 0u;
-        const uint32_t db = dtoff[s], nb = dlen[s];
-        if (na + nb > kThreadMerge) big[atomicAdd(nbig, 1u)] = uint32_t(s);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s - lane < nslot; s += stride) {
+        const bool valid = s < nslot;
+        uint32_t oa = 0, na = 0, db = 0, nb = 0;
+        if (valid) {
+            oa = off ? off[s] : 0u;
+            na = off ? off[s + 1] - oa : 0u;
+            db = dtoff[s];
+            nb = dlen[s];
+        }
+        warp_append(na + nb > kThreadMerge, uint32_t(s), big, nbig);
+        if (!valid) continue;
         if (na == 0 || nb == 0) {
             mlen[s] = na + nb;
             continue;

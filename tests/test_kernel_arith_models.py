@@ -269,37 +269,64 @@ def test_radix_select_keeps_exactly_the_k_smallest(seed):
 
 # ---------------------------------------------------------------- build: small-slot sort
 #
-# The build sorts and deduplicates each slot of at most eight cells in one
+# The build sorts and deduplicates each slot of at most sixteen cells in one
 # thread's registers with a fixed compare-exchange network (Batcher's odd-even
-# merge sort for eight inputs, nineteen comparators), padded with 0xFFFFFFFF.
-# By the 0-1 principle a network that sorts all 2^8 binary inputs sorts every
-# input; the dedupe then keeps the first of each run.
-
-NET8 = [(0, 1), (2, 3), (4, 5), (6, 7), (0, 2), (1, 3), (4, 6), (5, 7), (1, 2), (5, 6),
-        (0, 4), (1, 5), (2, 6), (3, 7), (2, 4), (3, 5), (1, 2), (3, 4), (5, 6)]
+# merge sort for sixteen inputs, 63 comparators; its first nineteen sort the
+# first eight inputs alone), padded with 0xFFFFFFFF. By the 0-1 principle a
+# network that sorts all binary inputs sorts every input; the dedupe then
+# keeps the first of each run. The network is read from the kernel's source.
 
 
-def net8_sort(vals):
-    v = list(vals) + [M32] * (8 - len(vals))
-    for i, j in NET8:
+def net_sort(vals):
+    net = kernel_network()
+    n = 8 if len(vals) <= 8 else 16
+    v = list(vals) + [M32] * (n - len(vals))
+    for i, j in (net[:19] if n == 8 else net):
         if v[i] > v[j]:
             v[i], v[j] = v[j], v[i]
     return v
-
-
-def test_sort_network_8_sorts_every_binary_input():
-    assert len(NET8) == 19
-    for m in range(256):
-        bits = [(m >> i) & 1 for i in range(8)]
-        assert net8_sort(bits) == sorted(bits)
 
 
 @pytest.mark.parametrize("seed", range(20))
 def test_small_slot_sort_and_dedupe(seed):
     rng = np.random.default_rng(900 + seed)
     for _ in range(200):
-        n = int(rng.integers(0, 9))
+        n = int(rng.integers(0, 17))
         vals = rng.integers(0, int(rng.choice([3, 20, 65536])), size=n).tolist()
-        v = net8_sort(vals)
+        v = net_sort(vals)
         out = [x for i, x in enumerate(v) if x != M32 and (i == 0 or x != v[i - 1])]
         assert out == sorted(set(vals))
+
+
+def kernel_network():
+    """The compare-exchange pairs of k_slot_unique_small, read from the source."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_2106_11565_gb300", "csrc", "build.cu")).read()
+    body = src[src.index("kNet16[63][2] = {"):]
+    body = body[:body.index("};")]
+    return [(int(a), int(b)) for a, b in re.findall(r"\{(\d+), (\d+)\}", body)]
+
+
+def test_kernel_network_sorts_16_and_its_prefix_sorts_8():
+    net = kernel_network()
+    assert len(net) == 63
+    # 0-1 principle, vectorised over all 2^16 binary inputs
+    m = np.arange(1 << 16, dtype=np.uint32)
+    v = ((m[:, None] >> np.arange(16, dtype=np.uint32)[None, :]) & 1).astype(np.uint8)
+    for i, j in net:
+        lo = np.minimum(v[:, i], v[:, j])
+        hi = np.maximum(v[:, i], v[:, j])
+        v[:, i], v[:, j] = lo, hi
+    assert np.all(np.diff(v.astype(np.int8), axis=1) >= 0)
+    # the first nineteen comparators touch only the first eight inputs and sort them
+    pre = net[:19]
+    assert all(i < 8 and j < 8 for i, j in pre)
+    m = np.arange(1 << 8, dtype=np.uint32)
+    v = ((m[:, None] >> np.arange(8, dtype=np.uint32)[None, :]) & 1).astype(np.uint8)
+    for i, j in pre:
+        lo = np.minimum(v[:, i], v[:, j])
+        hi = np.maximum(v[:, i], v[:, j])
+        v[:, i], v[:, j] = lo, hi
+    assert np.all(np.diff(v.astype(np.int8), axis=1) >= 0)
