@@ -1634,7 +1634,11 @@ def run_serving(args) -> dict:
     h_q4 = q4.cpu().pin_memory().numpy()
     sources = [sets_source(F, id2, c2["q"], 0.5, keep), dense_source(F, id4, h_q4, 0.5, keep)]
     rng = np.random.default_rng([c2["seed"], 55])
-    poff, pel = pool["off"], pool["elems"]
+    # the insert payloads live in page-locked host memory, as a serving
+    # client's buffers would (the library copies them by DMA)
+    poff = torch.from_numpy(pool["off"].view(np.int64)).pin_memory().numpy().view(np.uint64)
+    pel = torch.from_numpy(pool["elems"].view(np.int32)).pin_memory().numpy().view(np.uint32)
+    keep += [poff, pel]
     used = 0
     runs = {}
     clocks = ClockSampler(0)
@@ -1647,8 +1651,9 @@ def run_serving(args) -> dict:
         n_ins = int(round(np.exp(rng.uniform(np.log(1e3), np.log(1e5)))))
         n_ins = min(n_ins, len(poff) - 1)
         lo = used % (len(poff) - 1 - n_ins + 1)
-        off = (poff[lo:lo + n_ins + 1] - poff[lo]).astype(np.uint64)
-        el = np.ascontiguousarray(pel[poff[lo]:poff[lo + n_ins]])
+        off = torch.from_numpy((poff[lo:lo + n_ins + 1] - poff[lo]).astype(np.int64)).pin_memory().numpy() \
+            .view(np.uint64)
+        el = pel[poff[lo]:poff[lo + n_ins]]                  # a contiguous slice of the pinned pool
         fp = F.flinng_points()
         fp.off, fp.elems = off.ctypes.data, el.ctypes.data
         perm = WL.group_permutations(c2["seed"], c2["R"], n_ins, batch=100 + int(f * 100))

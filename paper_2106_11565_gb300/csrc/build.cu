@@ -521,13 +521,13 @@ int build_heavy(flinng_index *ix, void *scan_ws, uint32_t *list)
     const uint64_t words = uint64_t(nh) * ix->BRw;
     if (words > ix->hbm_words) {
         if (ix->hbm) {
-            cudaFree(ix->hbm);
+            FL_CUDA(cudaFreeAsync(ix->hbm, st));     // stream-ordered, as the workspace
             ix->device_bytes -= ix->hbm_words * 4;
             ix->hbm = nullptr;
             ix->hbm_words = 0;
         }
         const uint64_t want = words + words / 8 + ix->BRw;
-        FL_CUDA(cudaMalloc(&ix->hbm, want * 4));
+        FL_CUDA(cudaMallocAsync(&ix->hbm, want * 4, st));
         ix->hbm_words = want;
         ix->device_bytes += want * 4;
     }

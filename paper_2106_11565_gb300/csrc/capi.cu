@@ -64,15 +64,18 @@ int ensure_dyn_smem(const void *fn, size_t smem)
 int ws_reserve(flinng_index *ix, size_t bytes)
 {
     if (bytes <= ix->ws.bytes) return FLINNG_OK;
-    FL_CUDA(cudaStreamSynchronize(ix->stream));
+    // stream-ordered: the old workspace is released after the work already
+    // queued on the index's stream and the new one is ready for the next;
+    // unlike cudaFree this waits for no other stream (other indices, batches
+    // served on other streams)
     if (ix->ws.ptr) {
-        cudaFree(ix->ws.ptr);
+        FL_CUDA(cudaFreeAsync(ix->ws.ptr, ix->stream));
         ix->device_bytes -= ix->ws.bytes;
         ix->ws.ptr = nullptr;
         ix->ws.bytes = 0;
     }
     const size_t want = bytes + (bytes >> 3);
-    FL_CUDA(cudaMalloc(&ix->ws.ptr, want));
+    FL_CUDA(cudaMallocAsync(&ix->ws.ptr, want, ix->stream));
     ix->ws.bytes = want;
     ix->device_bytes += want;
     return FLINNG_OK;
