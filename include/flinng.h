@@ -234,6 +234,17 @@ uint64_t flinng_device_bytes(const flinng_index *idx);
 /* Set the stream used by subsequent calls (cudaStream_t or NULL). */
 int flinng_set_stream(flinng_index *idx, void *stream);
 
+/* Limit of each wait in the tensor-core SRP pipeline of this index (default
+ * 1,000,000,000 ns; 0 makes each wait a single try; UINT64_MAX restores the
+ * default). The paper has no counterpart: this exercises the failure path
+ * of the bounded waits. A wait that gives up makes the kernel stop issuing
+ * work, wait (with the default limit) for the copies and MMAs it issued,
+ * free its tensor memory and set the index's timeout flag, so the context
+ * stays usable; calls that synchronise (host buffers) return
+ * FLINNG_ERR_TIMEOUT at once, and every later hash or query of the index
+ * does. Errors: INVALID_ARG for NULL. */
+int flinng_set_tc_wait(flinng_index *idx, uint64_t limit_ns);
+
 /* How flinng_query runs a batch (same results in every mode):
  * FLINNG_QUERY_PLAIN - a hash kernel for the batch, then one count / decode /
  *   top-k kernel (one CTA per query);

@@ -465,6 +465,13 @@ int flinng_set_stream(flinng_index *idx, void *stream)
     return FLINNG_OK;
 }
 
+int flinng_set_tc_wait(flinng_index *idx, uint64_t limit_ns)
+{
+    if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
+    idx->tc_wait_ns = limit_ns + 1;     // 0 (the overflow of UINT64_MAX) keeps the default
+    return FLINNG_OK;
+}
+
 int flinng_set_query_mode(flinng_index *idx, uint32_t mode)
 {
     if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
@@ -630,6 +637,8 @@ int flinng_hash(flinng_index *idx, const flinng_points *pts, uint64_t n, uint32_
         if (out_values) FL_CUDA(cudaMemcpyAsync(out_values, v, n * P * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         if (out_proj) FL_CUDA(cudaMemcpyAsync(out_proj, pr, n * P * sizeof(float), cudaMemcpyDeviceToHost, st));
         FL_CUDA(cudaStreamSynchronize(st));
+        // the tensor-core pipeline's timeout flag has landed by now
+        if (srp && idx->h_flag[3]) return set_error(FLINNG_ERR_TIMEOUT, "tensor-core SRP: a pipeline wait timed out");
     }
     return FLINNG_OK;
 }
@@ -722,6 +731,7 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
                                         cudaMemcpyDeviceToHost, st));
         }
         FL_CUDA(cudaStreamSynchronize(st));
+        if (idx->h_flag[3]) return set_error(FLINNG_ERR_TIMEOUT, "tensor-core SRP: a pipeline wait timed out");
     }
     return FLINNG_OK;
 }

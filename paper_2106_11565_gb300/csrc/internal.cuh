@@ -107,6 +107,7 @@ struct flinng_index {
     float *w_norm;            // upper bounds of ||w_j||
     float *w_aux;             // single-term tensor forms: P upper bounds of ||w_j - q(w_j)||, then P row scales
     uint32_t *tc_err;         // tensor-core pipeline timeout flag
+    uint64_t tc_wait_ns;      // limit of the tensor-core pipeline's waits + 1 (0: the default)
 
     // shape
     uint32_t P;            // L * K projections / MinHash values per point

@@ -120,15 +120,17 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// Bounded wait: false if the phase has not completed within kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// Bounded wait: false if the phase has not completed within limit_ns
+// (0: a single try).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns = kWaitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
+    if (limit_ns == 0) return false;
     const uint64_t t0 = global_ns();
     for (;;) {
         for (int i = 0; i < 256; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -234,6 +236,7 @@ struct TcArgs {
     unsigned long long *rlist;
     unsigned long long *rcount;
     uint32_t *err;         // set to 1 on a wait timeout
+    uint64_t wait_ns;      // limit of the pipeline's waits (the drains after an abort keep kWaitNs)
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
@@ -297,7 +300,7 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
         if (lane == 0) {
             for (uint32_t kb = 0; kb < nkb; ++kb) {
                 const int s = kb % kStages;
-                if (kb >= uint32_t(kStages) && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) {
+                if (kb >= uint32_t(kStages) && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1, a.wait_ns)) {
                     atomicExch(abort_flag, 1u);
                     break;
                 }
@@ -317,8 +320,8 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
             for (uint32_t kb = 0; kb < nkb; ++kb) {
                 const int s = kb % kStages;
                 const uint32_t b = kb & 1u;
-                if (!mbar_wait(&full[s], (kb / kStages) & 1) ||
-                    (kb >= 2 && !mbar_wait(&tempty[b], ((kb >> 1) - 1) & 1))) {
+                if (!mbar_wait(&full[s], (kb / kStages) & 1, a.wait_ns) ||
+                    (kb >= 2 && !mbar_wait(&tempty[b], ((kb >> 1) - 1) & 1, a.wait_ns))) {
                     atomicExch(abort_flag, 1u);
                     break;
                 }
@@ -365,7 +368,7 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
         for (uint32_t kb = 0; kb < nkb; ++kb) {
             const uint32_t b = kb & 1u;
             uint32_t got = 0;
-            if (lane == 0) got = mbar_wait(&tfull[b], (kb >> 1) & 1) ? 1u : 0u;
+            if (lane == 0) got = mbar_wait(&tfull[b], (kb >> 1) & 1, a.wait_ns) ? 1u : 0u;
             got = __shfl_sync(0xffffffffu, got, 0);
             if (!got) {
                 if (lane == 0) atomicExch(abort_flag, 1u);
@@ -460,12 +463,12 @@ k_srp_tc(const __grid_constant__ CUtensorMap mx1, const __grid_constant__ CUtens
         // let the copies this CTA issued land before its shared memory goes away
         if (warp == 0 && lane == 0) {
             for (uint32_t kb = (issued > uint32_t(kStages) ? issued - kStages : 0); kb < issued; ++kb)
-                mbar_wait(&full[kb % kStages], (kb / kStages) & 1);
+                mbar_wait(&full[kb % kStages], (kb / kStages) & 1, kWaitNs);
         }
     }
     if (warp == 1) {
         // every MMA has completed before the columns are freed
-        if (lane == 0) mbar_wait(mdone, 0);
+        if (lane == 0) mbar_wait(mdone, 0, kWaitNs);
         __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(F::kTmemCols) : "memory");
@@ -798,6 +801,7 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
         a.rlist = list1;
         a.rcount = cnt;
         a.err = ix->tc_err;
+        a.wait_ns = ix->tc_wait_ns ? ix->tc_wait_ns - 1 : kWaitNs;
         if (prec == FLINNG_PREC_BF16X2) FL_TRY(launch_tc<kFormBf16x2>(mx1, mx2, mw1, mw2, a, rows, st));
         else if (prec == FLINNG_PREC_BF16) FL_TRY(launch_tc<kFormBf16>(mx1, mx2, mw1, mw2, a, rows, st));
         else FL_TRY(launch_tc<kFormFp8>(mx1, mx2, mw1, mw2, a, rows, st));

@@ -119,6 +119,7 @@ _SIGS = {
                                              C.c_void_p, C.c_uint64, C.c_void_p]),
     "flinng_query_noalloc": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint32, C.c_void_p,
                                        C.c_uint32, C.c_void_p, C.c_void_p]),
+    "flinng_set_tc_wait": (C.c_int, [C.c_void_p, C.c_uint64]),
 }
 
 _lib = None
@@ -456,6 +457,10 @@ class Index:
         ch = np.zeros(3, np.uint32)
         _check(self.lib.flinng_tune_query(self.h, C.byref(fp), nq, k_max, dev, ch.ctypes.data))
         return {"threads": int(ch[0]), "ctas_per_sm": int(ch[1]), "cap": int(ch[2])}
+
+    def set_tc_wait(self, limit_ns: int):
+        """Limit of each tensor-core pipeline wait (flinng_set_tc_wait)."""
+        _check(self.lib.flinng_set_tc_wait(self.h, limit_ns))
 
     def set_tuning(self, nq: int, threads: int, ctas_per_sm: int = 0, cap: int = 0):
         """Pin the fused query's launch shape for batches of nq's size class."""
