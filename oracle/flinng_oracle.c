@@ -351,6 +351,33 @@ void oracle_counts_direct(const uint32_t *bucket, const uint16_t *gid,
     free(hit);
 }
 
+/* Multi-probe counts (the multi-probe LSH idea the related work cites, as an
+ * option): in table l the query probes its own bucket and the P - 1 buckets
+ * that differ from it in exactly one of the code's bits 0 .. P-2 (SRP: the
+ * sign of projection l*K + j flipped). A cell counts table l once if some
+ * member's bucket in table l is one of those probes, so counts stay in
+ * [0, L]. P = 1 is oracle_counts_direct. */
+void oracle_counts_multiprobe(const uint32_t *bucket, const uint16_t *gid,
+                              uint64_t N, uint32_t L, uint32_t R, uint32_t B,
+                              const uint32_t *qbucket, uint32_t P, uint16_t *cnt)
+{
+    const uint32_t BR = B * R;
+    uint8_t *hit = (uint8_t *)malloc(BR ? BR : 1);
+    for (uint32_t c = 0; c < BR; ++c) cnt[c] = 0;
+    for (uint32_t l = 0; l < L; ++l) {
+        memset(hit, 0, BR ? BR : 1);
+        for (uint64_t x = 0; x < N; ++x) {
+            const uint32_t diff = bucket[x * L + l] ^ qbucket[l];
+            int probed = diff == 0;
+            for (uint32_t j = 0; j + 1 < P && !probed; ++j) probed = diff == (1u << j);
+            if (probed)
+                for (uint32_t r = 0; r < R; ++r) hit[r * B + gid[x * R + r]] = 1;
+        }
+        for (uint32_t c = 0; c < BR; ++c) cnt[c] += hit[c];
+    }
+    free(hit);
+}
+
 /* ------------------------------------------------------------------------ */
 /* A7-A9: Alg. 3, threshold relaxation                                       */
 /* ------------------------------------------------------------------------ */

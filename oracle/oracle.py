@@ -74,6 +74,9 @@ def lib():
         L.oracle_counts_direct.argtypes = [u32, u16, C.c_uint64, C.c_uint32, C.c_uint32,
                                            C.c_uint32, u32, u16]
         L.oracle_counts_direct.restype = None
+        L.oracle_counts_multiprobe.argtypes = [u32, u16, C.c_uint64, C.c_uint32, C.c_uint32,
+                                               C.c_uint32, u32, C.c_uint32, u16]
+        L.oracle_counts_multiprobe.restype = None
         L.oracle_alg3.argtypes = [u16, u64, u32, C.c_uint64, C.c_uint32, C.c_uint32,
                                   C.c_uint32, C.c_uint32, u32, u16, C.c_uint32]
         L.oracle_alg3.restype = C.c_uint32
@@ -195,6 +198,18 @@ def counts_direct(buckets, gid, B: int, qbucket):
     R = gid.shape[1]
     cnt = np.zeros(B * R, np.uint16)
     lib().oracle_counts_direct(buckets, gid, N, L, R, B, _c(qbucket, np.uint32), cnt)
+    return cnt
+
+
+def counts_multiprobe(buckets, gid, B: int, qbucket, P: int):
+    """Per-cell counts with P probes per table (the query's bucket and its
+    one-bit neighbours in bits 0 .. P-2), from the definition."""
+    buckets = _c(buckets, np.uint32)
+    gid = _c(gid, np.uint16)
+    N, L = buckets.shape
+    R = gid.shape[1]
+    cnt = np.zeros(B * R, np.uint16)
+    lib().oracle_counts_multiprobe(buckets, gid, N, L, R, B, _c(qbucket, np.uint32), P, cnt)
     return cnt
 
 
