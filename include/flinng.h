@@ -245,6 +245,21 @@ int flinng_set_stream(flinng_index *idx, void *stream);
  * does. Errors: INVALID_ARG for NULL. */
 int flinng_set_tc_wait(flinng_index *idx, uint64_t limit_ns);
 
+/* Multi-probe counting (cosine / SRP indices; the multi-probe LSH that the
+ * related work of Sec. 2 cites, as an option the paper does not use): with
+ * probes = P > 1, table l of a query probes its own bucket b_l and the P - 1
+ * buckets b_l ^ (1 << j), j = 0 .. P-2 (the sign of projection l*K + j
+ * flipped). A cell counts table l once if the list of any probed bucket of
+ * that table holds it, so counts stay in 0..L and Alg. 3 decodes them as
+ * usual; with P = 1 (the default; 0 means 1) every call is the paper's
+ * single-probe method. flinng_query and flinng_query_buckets then count with
+ * a separate kernel and decode from those counts (the fused and graph modes
+ * are not used for such an index; nq x B*R x 2 bytes of workspace), and
+ * flinng_counts returns the multi-probe counts. The server and
+ * flinng_query_noalloc reject such an index (INVALID_ARG).
+ * Errors: INVALID_ARG (NULL, a set index and P > 1, or P > K + 1). */
+int flinng_set_probes(flinng_index *idx, uint32_t probes);
+
 /* How flinng_query runs a batch (same results in every mode):
  * FLINNG_QUERY_PLAIN - a hash kernel for the batch, then one count / decode /
  *   top-k kernel (one CTA per query);
@@ -313,8 +328,9 @@ int flinng_query_buckets(flinng_index *idx, const uint32_t *qbuckets,
 
 /*
  * Per-cell collision counts of nq queries given their buckets (Sec. 5):
- * out_counts nq x (B*R) uint16 (each in 0..L). Buckets < 2^W, checked as in
- * flinng_query_buckets. Errors: INVALID_ARG, CUDA.
+ * out_counts nq x (B*R) uint16 (each in 0..L; the multi-probe counts when the
+ * index probes more than one bucket per table, see flinng_set_probes).
+ * Buckets < 2^W, checked as in flinng_query_buckets. Errors: INVALID_ARG, CUDA.
  */
 int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq,
                   uint16_t *out_counts, int on_device);

@@ -472,6 +472,17 @@ int flinng_set_tc_wait(flinng_index *idx, uint64_t limit_ns)
     return FLINNG_OK;
 }
 
+int flinng_set_probes(flinng_index *idx, uint32_t probes)
+{
+    if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
+    if (probes > 1 && idx->cfg.metric != FLINNG_COSINE_SRP)
+        return set_error(FLINNG_ERR_INVALID_ARG, "set_probes: multi-probe counting is defined for SRP codes only");
+    if (probes > idx->cfg.K + 1)
+        return set_error(FLINNG_ERR_INVALID_ARG, "set_probes: %u probes > K + 1 = %u", probes, idx->cfg.K + 1);
+    idx->probes = probes;
+    return FLINNG_OK;
+}
+
 int flinng_set_query_mode(flinng_index *idx, uint32_t mode)
 {
     if (!idx) return set_error(FLINNG_ERR_INVALID_ARG, "index is null");
@@ -658,7 +669,9 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
             if (k[i] > k_max) return set_error(FLINNG_ERR_INVALID_ARG, "query: k[%u] = %u > k_max", i, k[i]);
     const cudaStream_t st = idx->stream;
     const uint32_t L = idx->cfg.L;
+    const bool probe = idx->probes > 1;
     size_t need = 4096 + carve_bytes<uint32_t>(uint64_t(nq) * L);
+    if (probe) need += carve_bytes<uint16_t>(uint64_t(nq) * idx->BR);
     if (q) need += stage_bytes(idx, q, nq, on_device) + hash_ws_bytes(idx, nq);
     if (!on_device)
         need += carve_bytes<uint32_t>(nq) + carve_bytes<uint32_t>(uint64_t(nq) * k_max) +
@@ -669,7 +682,7 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
     // Per-CTA hashing reads all L*K projection rows for every query: for a
     // large projection matrix the batched GEMM (plain form) hashes far better.
     const bool big_srp = idx->cfg.metric == FLINNG_COSINE_SRP && uint64_t(idx->P) * idx->cfg.dim > (1ull << 18);
-    const bool fused = q && !big_srp &&
+    const bool fused = q && !big_srp && !probe &&
                        (idx->query_mode == FLINNG_QUERY_FUSED || idx->query_mode == FLINNG_QUERY_GRAPH);
     Staged fs;
     if (fused) {
@@ -720,6 +733,10 @@ static int query_common(flinng_index *idx, const flinng_points *q, const uint32_
             FL_TRY(query_graph_launch(idx, fq, dk, k_max, dids, dsc, tune));
         else
             FL_TRY(query_fused_launch(idx, fq, dk, k_max, dids, dsc, tune));
+    } else if (probe) {
+        uint16_t *cnt = c.take<uint16_t>(uint64_t(nq) * idx->BR);
+        FL_TRY(probe_counts_launch(idx, qb, nq, idx->probes, cnt));
+        FL_TRY(query_launch_counts(idx, nullptr, cnt, L, nq, dk, k_max, dids, dsc));
     } else {
         FL_TRY(query_launch(idx, qb, nq, dk, k_max, dids, dsc));
     }
@@ -814,14 +831,16 @@ int flinng_counts(flinng_index *idx, const uint32_t *qbuckets, uint32_t nq, uint
     if (!qbuckets || !out_counts) return set_error(FLINNG_ERR_INVALID_ARG, "counts: null buffer");
     const cudaStream_t st = idx->stream;
     const uint32_t L = idx->cfg.L, BR = idx->BR;
-    if (on_device) return counts_launch(idx, qbuckets, nq, out_counts);
+    const uint32_t P = idx->probes;
+    if (on_device)
+        return P > 1 ? probe_counts_launch(idx, qbuckets, nq, P, out_counts) : counts_launch(idx, qbuckets, nq, out_counts);
     FL_TRY(check_host_buckets(idx, qbuckets, uint64_t(nq) * L, "counts"));
     FL_TRY(ws_reserve(idx, carve_bytes<uint32_t>(uint64_t(nq) * L) + carve_bytes<uint16_t>(uint64_t(nq) * BR) + 1024));
     Carver c(idx->ws.ptr, idx->ws.bytes);
     uint32_t *qb = c.take<uint32_t>(uint64_t(nq) * L);
     uint16_t *oc = c.take<uint16_t>(uint64_t(nq) * BR);
     FL_CUDA(cudaMemcpyAsync(qb, qbuckets, uint64_t(nq) * L * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    FL_TRY(counts_launch(idx, qb, nq, oc));
+    FL_TRY(P > 1 ? probe_counts_launch(idx, qb, nq, P, oc) : counts_launch(idx, qb, nq, oc));
     FL_CUDA(cudaMemcpyAsync(out_counts, oc, uint64_t(nq) * BR * sizeof(uint16_t), cudaMemcpyDeviceToHost, st));
     FL_CUDA(cudaStreamSynchronize(st));
     return FLINNG_OK;

@@ -97,6 +97,7 @@ extern "C" int flinng_query_noalloc(flinng_index *idx, const flinng_points *q, u
     if (k_max > kMaxKMax) return set_error(FLINNG_ERR_INVALID_ARG, "query_noalloc: k_max > %u", kMaxKMax);
     if (nq == 0) return FLINNG_OK;
     if (!q || !out_ids) return set_error(FLINNG_ERR_INVALID_ARG, "query_noalloc: null q or out_ids");
+    if (idx->probes > 1) return set_error(FLINNG_ERR_INVALID_ARG, "query_noalloc: multi-probe counting needs a workspace");
     const bool srp = idx->cfg.metric == FLINNG_COSINE_SRP;
     if (srp ? (!q->x || q->ld < idx->cfg.dim) : (!q->off || !q->elems))
         return set_error(FLINNG_ERR_INVALID_ARG, "query_noalloc: bad points");

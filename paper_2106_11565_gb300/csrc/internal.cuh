@@ -146,6 +146,7 @@ struct flinng_index {
     flinng::Workspace ws;
     uint64_t device_bytes;
     uint32_t query_mode;   // FLINNG_QUERY_PLAIN, _FUSED or _GRAPH
+    uint32_t probes;       // buckets probed per table (0 or 1: the query's own only)
     int sms;               // multiprocessors of the device (0: not looked up yet)
     flinng::OccEntry occ[8];          // occupancy of recent fused launch shapes
     uint32_t n_occ;
@@ -224,5 +225,11 @@ int query_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
                  uint16_t *out_scores, const uint32_t *out_row = nullptr);
 int counts_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
                   uint16_t *out_counts);
+
+// ---- probe.cu
+// Multi-probe counts (probes P >= 1 per table): nq x B*R uint16, each <= L.
+size_t probe_smem_bytes(uint32_t BR);
+int probe_counts_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq, uint32_t P,
+                        uint16_t *out_counts);
 
 }  // namespace flinng

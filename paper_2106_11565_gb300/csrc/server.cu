@@ -243,6 +243,7 @@ int launch_batch(flinng_server *srv, Slot &slot, const flinng_request *reqs, uin
         if (in_bytes)
             FL_CUDA(cudaMemcpyAsync(d + Lo.in_el, h + Lo.in_el, in_bytes, cudaMemcpyHostToDevice, slot.stream));
     }
+    if (ix->probes > 1) return set_error(FLINNG_ERR_INVALID_ARG, "server: multi-probe indices are not served");
     // bind the slot's stream and scratch to the index for these launches
     const cudaStream_t s0 = ix->stream;
     uint32_t *qn0 = ix->qnext;
@@ -354,6 +355,7 @@ int flinng_server_destroy(flinng_server *srv)
 int flinng_server_add_index(flinng_server *srv, flinng_index *ix, uint32_t *index_id)
 {
     if (!srv || !ix) return set_error(FLINNG_ERR_INVALID_ARG, "server: null argument");
+    if (ix->probes > 1) return set_error(FLINNG_ERR_INVALID_ARG, "server: multi-probe indices are not served");
     const uint32_t L0 = srv->max_L, d0 = srv->max_dim;
     const uint64_t P0 = srv->max_P;
     if (ix->cfg.L > srv->max_L) srv->max_L = ix->cfg.L;

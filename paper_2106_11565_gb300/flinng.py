@@ -120,6 +120,7 @@ _SIGS = {
     "flinng_query_noalloc": (C.c_int, [C.c_void_p, C.POINTER(flinng_points), C.c_uint32, C.c_void_p,
                                        C.c_uint32, C.c_void_p, C.c_void_p]),
     "flinng_set_tc_wait": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "flinng_set_probes": (C.c_int, [C.c_void_p, C.c_uint32]),
 }
 
 _lib = None
@@ -461,6 +462,10 @@ class Index:
     def set_tc_wait(self, limit_ns: int):
         """Limit of each tensor-core pipeline wait (flinng_set_tc_wait)."""
         _check(self.lib.flinng_set_tc_wait(self.h, limit_ns))
+
+    def set_probes(self, probes: int):
+        """Buckets probed per table (flinng_set_probes; 1 = single probe)."""
+        _check(self.lib.flinng_set_probes(self.h, probes))
 
     def set_tuning(self, nq: int, threads: int, ctas_per_sm: int = 0, cap: int = 0):
         """Pin the fused query's launch shape for batches of nq's size class."""
