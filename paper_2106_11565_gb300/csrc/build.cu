@@ -586,6 +586,9 @@ uint64_t worklist_entries(const flinng_index *ix, uint64_t n, bool reset)
 
 size_t insert_workspace_bytes(const flinng_index *ix, uint64_t n, bool reset)
 {
+    if (!reset && delta_insert_applies(ix, n))
+        return carve_bytes<uint32_t>(ix->BR + 1) +
+               std::max(delta_workspace_bytes(ix, n), scan_workspace_bytes(size_t(ix->BR) + 1)) + 256;
     const size_t ns = ix->nslot + 1;
     const size_t big = ns > size_t(ix->BR) + 1 ? ns : size_t(ix->BR) + 1;
     const uint64_t D = n * ix->cfg.L * ix->cfg.R;
@@ -609,28 +612,17 @@ int check_groups(flinng_index *ix, const uint16_t *groups, uint64_t n)
     return FLINNG_OK;
 }
 
-int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *perm, const uint16_t *groups,
-                  uint64_t n, void *ws)
-{
-    const cudaStream_t st = ix->stream;
-    const uint32_t R = ix->cfg.R, B = ix->cfg.B, L = ix->cfg.L, W = ix->cfg.range_bits;
-    const uint32_t BR = ix->BR, rp = ix->rp;
-    const uint64_t n_old = ix->n_points, N = n_old + n, nslot = ix->nslot;
-    const bool have_old = ix->n_cells > 0;
-    const uint64_t D = n * L * R;   // new (table, cell) entries before deduplication
-    Carver c(ws, ~size_t(0));
-    uint32_t *dtoff = c.take<uint32_t>(nslot + 1);     // new entries of slot s start here
-    uint32_t *cursor = c.take<uint32_t>(nslot + 1);    // scatter cursors, then merged lengths
-    uint32_t *mcur = c.take<uint32_t>(BR + 1);
-    uint32_t *work = c.take<uint32_t>(worklist_entries(ix, n, !have_old));
-    uint32_t *cnt = c.take<uint32_t>(4);
-    // the new entries: in the build scratch for a build from scratch, in the
-    // workspace for an insert (the scratch then receives the merged lists)
-    uint16_t *dbuf = have_old ? c.take<uint16_t>(D) : ix->cells_tmp;
-    void *scan_ws = c.base + ((c.used + 255) & ~size_t(255));
+namespace {
 
-    // groups of the new points: Alg. 1 from the permutations, or given outright
-    TraceRange stage1("groups and member lists");
+// Groups of the n new points (Alg. 1 from the permutations, or given
+// outright) and the member lists and records of all cells.
+int member_stage(flinng_index *ix, const uint32_t *perm, const uint16_t *groups, uint64_t n, uint32_t *mcur,
+                 void *scan_ws)
+{
+    TraceRange trace_("groups and member lists");
+    const cudaStream_t st = ix->stream;
+    const uint32_t R = ix->cfg.R, B = ix->cfg.B, BR = ix->BR, rp = ix->rp;
+    const uint64_t n_old = ix->n_points, N = n_old + n;
     if (n > 0) {
         if (groups)
             k_groups_given<<<thread_blocks(uint64_t(R) * n), 256, 0, st>>>(groups, R, n, n_old, rp, ix->gid);
@@ -656,10 +648,42 @@ int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *per
         count_launch();
         FL_CUDA(cudaGetLastError());
     }
+    return FLINNG_OK;
+}
 
-    stage1.end();
-    TraceRange stage2("reverse index");
-    // 1. the new entries by slot: counting sort (histogram, scan, scatter)
+}  // namespace
+
+int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *perm, const uint16_t *groups,
+                  uint64_t n, void *ws)
+{
+    const cudaStream_t st = ix->stream;
+    const uint32_t R = ix->cfg.R, B = ix->cfg.B, L = ix->cfg.L, W = ix->cfg.range_bits;
+    const uint32_t BR = ix->BR, rp = ix->rp;
+    const uint64_t n_old = ix->n_points, N = n_old + n, nslot = ix->nslot;
+    const bool have_old = ix->n_cells > 0;
+    const uint64_t D = n * L * R;   // new (table, cell) entries before deduplication
+    const bool delta = delta_insert_applies(ix, n);
+    Carver c(ws, ~size_t(0));
+    uint32_t *mcur = c.take<uint32_t>(BR + 1);
+    if (delta) {
+        // a small batch: only the slots that gain cells are merged
+        void *dws = c.base + ((c.used + 255) & ~size_t(255));
+        FL_TRY(member_stage(ix, perm, groups, n, mcur, dws));
+        TraceRange stage2("reverse index (delta)");
+        return insert_delta(ix, buckets, n, dws);
+    }
+    uint32_t *dtoff = c.take<uint32_t>(nslot + 1);     // new entries of slot s start here
+    uint32_t *cursor = c.take<uint32_t>(nslot + 1);    // scatter cursors, then merged lengths
+    uint32_t *work = c.take<uint32_t>(worklist_entries(ix, n, !have_old));
+    uint32_t *cnt = c.take<uint32_t>(4);
+    // the new entries: in the build scratch for a build from scratch, in the
+    // workspace for an insert (the scratch then receives the merged lists)
+    uint16_t *dbuf = have_old ? c.take<uint16_t>(D) : ix->cells_tmp;
+    void *scan_ws = c.base + ((c.used + 255) & ~size_t(255));
+
+    FL_TRY(member_stage(ix, perm, groups, n, mcur, scan_ws));
+
+    TraceRange stage2("reverse index");    // 1. the new entries by slot: counting sort (histogram, scan, scatter)
     uint32_t *hist = ix->slot_a;
     FL_CUDA(cudaMemsetAsync(hist, 0, (nslot + 1) * sizeof(uint32_t), st));
     FL_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(uint32_t), st));

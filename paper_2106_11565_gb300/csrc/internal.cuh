@@ -226,6 +226,16 @@ int query_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
 int counts_launch(flinng_index *ix, const uint32_t *qbuckets, uint32_t nq,
                   uint16_t *out_counts);
 
+// ---- insert_delta.cu
+// An insert of n points into a built index merges only the slots that gain
+// cells when n * R <= kDeltaMaxKeys (the batch's entries of one table are
+// sorted in shared memory); larger batches take the full merge of build.cu.
+constexpr uint32_t kDeltaMaxKeys = 8192;
+bool delta_insert_applies(const flinng_index *ix, uint64_t n);
+size_t delta_workspace_bytes(const flinng_index *ix, uint64_t n);
+// After insert_hashed's group and member-list stage: the reverse index.
+int insert_delta(flinng_index *ix, const uint32_t *buckets, uint64_t n, void *ws);
+
 // ---- probe.cu
 // Multi-probe counts (probes P >= 1 per table): nq x B*R uint16, each <= L.
 size_t probe_smem_bytes(uint32_t BR);
