@@ -103,6 +103,9 @@ void free_index(flinng_index *ix)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ix->h_flag) cudaFreeHost(ix->h_flag);
+    if (ix->ev_fork) cudaEventDestroy(ix->ev_fork);
+    if (ix->ev_join) cudaEventDestroy(ix->ev_join);
+    if (ix->side) cudaStreamDestroy(ix->side);
     delete ix;
 }
 
@@ -434,6 +437,10 @@ int flinng_create(const flinng_config *cfg, const flinng_params *params, void *s
         chk(cudaMemsetAsync(ix->moff, 0, (size_t(ix->BR) + 1) * sizeof(uint32_t), st), "zero moff");
         chk(cudaMemsetAsync(ix->stats, 0, kStats * sizeof(unsigned long long), st), "zero stats");
         chk(cudaMemsetAsync(ix->tc_err, 0, 4, st), "zero tensor-core flag");
+        // the insert's second stream and its fork / join events
+        chk(cudaStreamCreateWithFlags(&ix->side, cudaStreamNonBlocking), "create side stream");
+        chk(cudaEventCreateWithFlags(&ix->ev_fork, cudaEventDisableTiming), "create event");
+        chk(cudaEventCreateWithFlags(&ix->ev_join, cudaEventDisableTiming), "create event");
         if (rc == FLINNG_OK && cfg->precision != FLINNG_PREC_FP32) rc = srp_tc_prepare_weights(ix);
         chk(cudaStreamSynchronize(st), "create sync");
     }

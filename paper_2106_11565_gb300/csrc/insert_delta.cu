@@ -14,13 +14,15 @@
 //     slots of all tables out in slot order: gslot[j], gdbeg[j] (added cells
 //     before touched slot j, over the whole index), gbeg[j] / gend[j] (the old
 //     extent of its list), and the added cells gdcell in the same order.
-//  3. k_delta_offsets: new off[s] = off[s] + gdbeg[first touched slot >= s].
-//  4. k_delta_move: the untouched lists between two touched slots, a run of
-//     old entries, move together by the cells added before them.
-//  5. k_delta_merge, a warp per touched slot: the union of its old and added
-//     cells (disjoint, both sorted) written at its new offset, each element at
-//     its own index plus its rank in the other list; cell bitmaps of heavy
-//     slots get the added cells; slots that become heavy are listed.
+//  3. new off[s] = off[s] + gdbeg[first touched slot >= s], and
+//  4. the untouched lists between two touched slots, a run of old entries,
+//     move together by the cells added before them: both passes in one
+//     launch, k_delta_stream, their chunks interleaved.
+//  5. k_delta_merge, a warp per touched slot, on a second stream beside 3-4
+//     (it writes only the touched slots' lists): the union of its old and
+//     added cells (disjoint, both sorted) written at its new offset, each
+//     element at its own index plus its rank in the other list; cell bitmaps
+//     of heavy slots get the added cells; slots that become heavy are listed.
 //  6. New bitmaps for the listed slots (the host grows the bitmap array first).
 #include <algorithm>
 #include <utility>
@@ -98,10 +100,9 @@ __device__ __forceinline__ uint32_t rank_u16(const uint16_t *a, uint32_t n, uint
 }
 
 // Step 1. Keys are (bucket << CB) | cell (CB bits hold a cell id), 32-bit
-// when W + CB <= 31; P2 (a power of two >= n R) of them in shared memory.
-// Each thread owns E = P2 / blockDim consecutive keys (or one, for P2 <
-// blockDim) in the compaction passes.
-template <class KT>
+// when W + CB <= 31; P2 (a power of two, 32 .. 32 E blockDim, >= n R) of
+// them in shared memory, E = max(1, P2 / blockDim) per thread.
+template <class KT, int E>
 __global__ void __launch_bounds__(kDeltaThreads)
 k_delta_table(const uint32_t *__restrict__ buckets, const uint16_t *__restrict__ gid, uint64_t n_old, uint32_t n,
               uint32_t L, uint32_t W, uint32_t R, uint32_t B, uint32_t rp, uint32_t P2, uint32_t CB,
@@ -125,23 +126,78 @@ k_delta_table(const uint32_t *__restrict__ buckets, const uint16_t *__restrict__
         key[i] = k;
     }
     __syncthreads();
+    // Bitonic sort. Warp w holds keys w 32 E .. (w + 1) 32 E - 1, lane-major
+    // (key e 32 + lane of its block in register e): compare-exchanges at
+    // distance < 32 are warp shuffles, at distance < 32 E between registers,
+    // and only the longer ones go through shared memory.
+    const uint32_t warp = tid >> 5, lane = tid & 31;
+    const bool active = warp * 32 * E < P2;
+    const uint32_t base = warp * 32 * E;
+    KT v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = active ? key[base + e * 32 + lane] : kNone;
     for (uint32_t k2 = 2; k2 <= P2; k2 <<= 1) {
-        for (uint32_t j = k2 >> 1; j > 0; j >>= 1) {
-            for (uint32_t i = tid; i < P2; i += nt) {
-                const uint32_t p = i ^ j;
-                if (p > i) {
-                    const KT x = key[i], y = key[p];
+        uint32_t j = k2 >> 1;
+        if (j >= 32u * E) {
+            if (active) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) key[base + e * 32 + lane] = v[e];
+            }
+            __syncthreads();
+            for (; j >= 32u * E; j >>= 1) {
+                for (uint32_t i = tid; i < P2; i += nt) {
+                    const uint32_t p = i ^ j;
+                    if (p > i) {
+                        const KT x = key[i], y = key[p];
+                        if ((x > y) == ((i & k2) == 0)) {
+                            key[i] = y;
+                            key[p] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            if (active) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) v[e] = key[base + e * 32 + lane];
+            }
+        }
+        if (!active) continue;
+#pragma unroll
+        for (int jj = E / 2; jj >= 1; jj >>= 1) {      // distance 32 jj: registers e and e ^ jj
+            if (j != 32u * jj) continue;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int p = e ^ jj;
+                if (p > e) {
+                    const uint32_t i = base + e * 32 + lane;
+                    const KT x = v[e], y = v[p];
                     if ((x > y) == ((i & k2) == 0)) {
-                        key[i] = y;
-                        key[p] = x;
+                        v[e] = y;
+                        v[p] = x;
                     }
                 }
             }
-            __syncthreads();
+            j >>= 1;
+        }
+        for (; j > 0; j >>= 1) {                       // distance < 32: lanes
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const uint32_t i = base + e * 32 + lane;
+                const KT o = __shfl_xor_sync(0xffffffffu, v[e], j);
+                const bool up = (i & k2) == 0, lower = (lane & j) == 0;
+                v[e] = (lower == up) ? (v[e] < o ? v[e] : o) : (v[e] < o ? o : v[e]);
+            }
         }
     }
-    // keep the first of equal keys whose cell the slot's old list lacks
-    const uint32_t E = P2 > nt ? P2 / nt : 1u;
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) key[base + e * 32 + lane] = v[e];
+    }
+    __syncthreads();
+    // keep the first of equal keys whose cell the slot's old list lacks; each
+    // thread now takes E consecutive keys
     const uint32_t i0 = tid * E;
     KT mine[8];
     uint32_t keepm = 0, cnt = 0;
@@ -242,44 +298,57 @@ __global__ void k_delta_chunks(const uint32_t *__restrict__ gslot, const uint32_
 }
 
 // Step 3, over slots 0 .. nslot (the offsets' nslot + 1 entries), four
-// slots per 16-byte access. A CTA's slots [s0, s1) meet the touched slots
-// j0 .. j1 - 1, which it stages in shared memory with gdbeg[j1].
-__global__ void k_delta_offsets(const uint32_t *__restrict__ off, uint64_t nslot, const uint32_t *__restrict__ gslot,
-                                const uint32_t *__restrict__ gdbeg, const uint32_t *__restrict__ off_j,
-                                uint32_t *__restrict__ noff)
+// slots per 16-byte access. Chunk c's slots [s0, s1) meet the touched slots
+// j0 .. j1 - 1, which it stages in shared memory with gdbeg[j1] (when fewer
+// than kStage; else it searches them in place).
+constexpr uint32_t kStage = 1024;     // touched slots a chunk stages in shared memory
+
+__device__ void delta_offsets(uint32_t c, uint32_t *sgs, uint32_t *sgd, const uint32_t *__restrict__ off,
+                              uint64_t nslot, const uint32_t *__restrict__ gslot, const uint32_t *__restrict__ gdbeg,
+                              const uint32_t *__restrict__ off_j, uint32_t *__restrict__ noff)
 {
-    __shared__ uint32_t sgs[kChunk + 1], sgd[kChunk + 1];
-    const uint64_t s0 = uint64_t(blockIdx.x) * kChunk;
+    const uint64_t s0 = uint64_t(c) * kChunk;
     const uint64_t s1 = s0 + kChunk < nslot + 1 ? s0 + kChunk : nslot + 1;
     // off_j[c + 1] is the first touched slot >= s1 (the total past the last chunk)
-    const uint32_t j0 = off_j[blockIdx.x], nj = off_j[blockIdx.x + 1] - j0;   // nj <= s1 - s0
-    for (uint32_t t = threadIdx.x; t <= nj; t += blockDim.x) {
-        sgs[t] = gslot[j0 + t];
-        sgd[t] = gdbeg[j0 + t];
+    const uint32_t j0 = off_j[c], nj = off_j[c + 1] - j0;   // nj <= s1 - s0
+    const bool staged = nj < kStage;
+    if (staged) {
+        for (uint32_t t = threadIdx.x; t <= nj; t += blockDim.x) {
+            sgs[t] = gslot[j0 + t];
+            sgd[t] = gdbeg[j0 + t];
+        }
     }
     __syncthreads();
-    // added cells before slot s: sgd[first staged index with sgs >= s]
-    auto shift = [&](uint32_t s) {
+    // first touched index >= j0 (relative) with gslot >= s, and the shift there
+    auto first_at = [&](uint32_t s) {
         uint32_t lo = 0, hi = nj;
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
-            if (sgs[mid] < s) lo = mid + 1;
+            if ((staged ? sgs[mid] : gslot[j0 + mid]) < s) lo = mid + 1;
             else hi = mid;
         }
-        return sgd[lo];
+        return lo;
     };
+    auto slot_at = [&](uint32_t t) { return staged ? sgs[t] : gslot[j0 + t]; };   // t <= nj: sentinel past the end
+    auto shift_at = [&](uint32_t t) { return staged ? sgd[t] : gdbeg[j0 + t]; };
     const uint32_t nv = uint32_t((s1 - s0) / 4);
     for (uint32_t v = threadIdx.x; v < nv; v += blockDim.x) {
         const uint64_t s = s0 + uint64_t(v) * 4;
         uint4 x = *reinterpret_cast<const uint4 *>(off + s);
-        x.x += shift(uint32_t(s));
-        x.y += shift(uint32_t(s + 1));
-        x.z += shift(uint32_t(s + 2));
-        x.w += shift(uint32_t(s + 3));
+        uint32_t t = first_at(uint32_t(s));
+        // slots s .. s + 3 share the shift unless a touched slot lies among s .. s + 2
+        uint32_t sh = shift_at(t);
+        x.x += sh;
+        if (t < nj && slot_at(t) == uint32_t(s)) sh = shift_at(++t);
+        x.y += sh;
+        if (t < nj && slot_at(t) == uint32_t(s + 1)) sh = shift_at(++t);
+        x.z += sh;
+        if (t < nj && slot_at(t) == uint32_t(s + 2)) sh = shift_at(++t);
+        x.w += sh;
         *reinterpret_cast<uint4 *>(noff + s) = x;
     }
     for (uint64_t s = s0 + uint64_t(nv) * 4 + threadIdx.x; s < s1; s += blockDim.x)
-        noff[s] = off[s] + shift(uint32_t(s));
+        noff[s] = off[s] + shift_at(first_at(uint32_t(s)));
 }
 
 // Step 4, over the old entries, kChunk per CTA. Between touched slots j - 1
@@ -290,12 +359,12 @@ __global__ void k_delta_offsets(const uint32_t *__restrict__ off, uint64_t nslot
 // mov_lo[c] with a cursor, its entries being in increasing order.
 constexpr int kMoveWords = kChunk / 512;     // 32-bit words (two entries) per thread
 
-__global__ void __launch_bounds__(256)
-k_delta_move(const uint16_t *__restrict__ cells, uint64_t n_cells, const uint32_t *__restrict__ gbeg,
-             const uint32_t *__restrict__ gend, const uint32_t *__restrict__ gdbeg,
-             const uint32_t *__restrict__ mov_lo, uint16_t *__restrict__ out)
+__device__ void delta_move(uint32_t c, const uint16_t *__restrict__ cells, uint64_t n_cells,
+                           const uint32_t *__restrict__ gbeg, const uint32_t *__restrict__ gend,
+                           const uint32_t *__restrict__ gdbeg, const uint32_t *__restrict__ mov_lo,
+                           uint16_t *__restrict__ out)
 {
-    const uint64_t i0 = uint64_t(blockIdx.x) * kChunk;      // even: words are 4-byte aligned
+    const uint64_t i0 = uint64_t(c) * kChunk;      // even: words are 4-byte aligned
     const uint32_t *cw = reinterpret_cast<const uint32_t *>(cells + i0);
     uint32_t v[kMoveWords];
 #pragma unroll
@@ -305,7 +374,7 @@ k_delta_move(const uint16_t *__restrict__ cells, uint64_t n_cells, const uint32_
         if (i + 1 < n_cells) v[k] = cw[uint64_t(k) * 256 + threadIdx.x];
         else if (i < n_cells) v[k] = cells[i];
     }
-    uint32_t j = mov_lo[blockIdx.x];
+    uint32_t j = mov_lo[c];
     uint32_t e = gend[j], b = gbeg[j], sh = gdbeg[j];      // kEmpty32 past the last touched slot
 #pragma unroll
     for (int k = 0; k < 2 * kMoveWords; ++k) {
@@ -319,6 +388,26 @@ k_delta_move(const uint16_t *__restrict__ cells, uint64_t n_cells, const uint32_
         }
         if (i < b) out[i + sh] = uint16_t(v[k >> 1] >> (16 * (k & 1)));
     }
+}
+
+// Steps 3 and 4 in one launch, their chunks interleaved in proportion so that
+// both streams run side by side: block b is an offsets chunk when
+// floor((b + 1) nc_off / nb) > floor(b nc_off / nb), its index then
+// floor(b nc_off / nb); else a move chunk of index b - floor((b + 1) nc_off / nb).
+__global__ void __launch_bounds__(256)
+k_delta_stream(uint32_t nc_off, uint32_t nc_mov, const uint32_t *__restrict__ off, uint64_t nslot,
+               const uint32_t *__restrict__ gslot, const uint32_t *__restrict__ gdbeg,
+               const uint32_t *__restrict__ off_j, uint32_t *__restrict__ noff, const uint16_t *__restrict__ cells,
+               uint64_t n_cells, const uint32_t *__restrict__ gbeg, const uint32_t *__restrict__ gend,
+               const uint32_t *__restrict__ mov_lo, uint16_t *__restrict__ out)
+{
+    __shared__ uint32_t sgs[kStage], sgd[kStage];
+    const uint64_t nb = uint64_t(nc_off) + nc_mov, b = blockIdx.x;
+    const uint64_t before = b * nc_off / nb, upto = (b + 1) * nc_off / nb;
+    if (upto > before)
+        delta_offsets(uint32_t(before), sgs, sgd, off, nslot, gslot, gdbeg, off_j, noff);
+    else
+        delta_move(uint32_t(b - upto), cells, n_cells, gbeg, gend, gdbeg, mov_lo, out);
 }
 
 // Step 5, a warp per touched slot.
@@ -397,6 +486,26 @@ inline unsigned blocks_of(uint64_t items, uint64_t per)
     return unsigned(b ? b : 1);
 }
 
+template <class KT, int E, class... Args>
+int launch_table_e(uint32_t grid, uint32_t P2, cudaStream_t st, Args... args)
+{
+    const size_t smem = size_t(P2) * sizeof(KT) + 32 * 4;
+    FL_TRY(ensure_dyn_smem((const void *)k_delta_table<KT, E>, smem));
+    k_delta_table<KT, E><<<grid, kDeltaThreads, smem, st>>>(args...);
+    return FLINNG_OK;
+}
+
+template <class KT, class... Args>
+int launch_table(int E, uint32_t grid, uint32_t P2, cudaStream_t st, Args... args)
+{
+    switch (E) {
+    case 8: return launch_table_e<KT, 8>(grid, P2, st, args...);
+    case 4: return launch_table_e<KT, 4>(grid, P2, st, args...);
+    case 2: return launch_table_e<KT, 2>(grid, P2, st, args...);
+    default: return launch_table_e<KT, 1>(grid, P2, st, args...);
+    }
+}
+
 }  // namespace
 
 bool delta_insert_applies(const flinng_index *ix, uint64_t n)
@@ -436,20 +545,16 @@ int insert_delta(flinng_index *ix, const uint32_t *buckets, uint64_t n, void *ws
     uint32_t *cnt = c.take<uint32_t>(4);
     void *scan_ws = c.base + ((c.used + 255) & ~size_t(255));
 
-    const uint32_t P2 = pow2_ceil(nR);
+    const uint32_t P2 = pow2_ceil(nR < 32 ? 32u : nR);
     uint32_t CB = 1;
     while ((1u << CB) < ix->BR) ++CB;
-    if (W + CB <= 31) {      // all-ones marks padding: real keys stay below it
-        const size_t smem = size_t(P2) * 4 + 32 * 4;
-        FL_TRY(ensure_dyn_smem((const void *)k_delta_table<uint32_t>, smem));
-        k_delta_table<uint32_t><<<L, kDeltaThreads, smem, st>>>(buckets, ix->gid, n_old, uint32_t(n), L, W, R, B,
-                                                                ix->rp, P2, CB, ix->off, ix->cells, rcell, rt, A, T);
-    } else {
-        const size_t smem = size_t(P2) * 8 + 32 * 4;
-        FL_TRY(ensure_dyn_smem((const void *)k_delta_table<uint64_t>, smem));
-        k_delta_table<uint64_t><<<L, kDeltaThreads, smem, st>>>(buckets, ix->gid, n_old, uint32_t(n), L, W, R, B,
-                                                                ix->rp, P2, CB, ix->off, ix->cells, rcell, rt, A, T);
-    }
+    const int E = P2 >= 8192 ? 8 : P2 >= 4096 ? 4 : P2 >= 2048 ? 2 : 1;
+    if (W + CB <= 31)        // all-ones marks padding: real keys stay below it
+        FL_TRY(launch_table<uint32_t>(E, L, P2, st, buckets, ix->gid, n_old, uint32_t(n), L, W, R, B, ix->rp, P2,
+                                      CB, ix->off, ix->cells, rcell, rt, A, T));
+    else
+        FL_TRY(launch_table<uint64_t>(E, L, P2, st, buckets, ix->gid, n_old, uint32_t(n), L, W, R, B, ix->rp, P2,
+                                      CB, ix->off, ix->cells, rcell, rt, A, T));
     count_launch();
     FL_CUDA(cudaGetLastError());
     FL_TRY(scan_exclusive(A, Apre, L, scan_ws, st));
@@ -463,17 +568,27 @@ int insert_delta(flinng_index *ix, const uint32_t *buckets, uint64_t n, void *ws
         gslot, gend, Tpre, L, nslot, n_cells, nc_off, nc_mov, off_j, mov_lo);
     count_launch();
     FL_CUDA(cudaGetLastError());
-    k_delta_offsets<<<nc_off, 256, 0, st>>>(ix->off, nslot, gslot, gdbeg, off_j, noff);
-    count_launch();
-    FL_CUDA(cudaGetLastError());
-    k_delta_move<<<nc_mov, 256, 0, st>>>(ix->cells, n_cells, gbeg, gend, gdbeg, mov_lo, ix->cells_tmp);
-    count_launch();
-    FL_CUDA(cudaGetLastError());
+    // the merge writes only the touched slots' new lists, the streaming passes
+    // only the other lists and the offsets: the merge runs beside them
     FL_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(uint32_t), st));
-    k_delta_merge<<<152 * 16, kWarps * 32, 0, st>>>(ix->off, ix->cells, gslot, gdbeg, gdcell, Tpre, L, ix->heavy_min,
-                                                   ix->hidx, ix->hbm, ix->BRw, ix->cells_tmp, newh, cnt);
+    if (!ix->side) {
+        FL_CUDA(cudaStreamCreateWithFlags(&ix->side, cudaStreamNonBlocking));
+        FL_CUDA(cudaEventCreateWithFlags(&ix->ev_fork, cudaEventDisableTiming));
+        FL_CUDA(cudaEventCreateWithFlags(&ix->ev_join, cudaEventDisableTiming));
+    }
+    FL_CUDA(cudaEventRecord(ix->ev_fork, st));
+    FL_CUDA(cudaStreamWaitEvent(ix->side, ix->ev_fork, 0));
+    k_delta_merge<<<152 * 16, kWarps * 32, 0, ix->side>>>(ix->off, ix->cells, gslot, gdbeg, gdcell, Tpre, L,
+                                                         ix->heavy_min, ix->hidx, ix->hbm, ix->BRw, ix->cells_tmp,
+                                                         newh, cnt);
     count_launch();
     FL_CUDA(cudaGetLastError());
+    FL_CUDA(cudaEventRecord(ix->ev_join, ix->side));
+    k_delta_stream<<<nc_off + nc_mov, 256, 0, st>>>(nc_off, nc_mov, ix->off, nslot, gslot, gdbeg, off_j, noff,
+                                                     ix->cells, n_cells, gbeg, gend, mov_lo, ix->cells_tmp);
+    count_launch();
+    FL_CUDA(cudaGetLastError());
+    FL_CUDA(cudaStreamWaitEvent(st, ix->ev_join, 0));
     // added cells and slots that became heavy
     FL_CUDA(cudaMemcpyAsync(ix->h_flag, Apre + L, 4, cudaMemcpyDeviceToHost, st));
     FL_CUDA(cudaMemcpyAsync(ix->h_flag + 1, cnt, 4, cudaMemcpyDeviceToHost, st));

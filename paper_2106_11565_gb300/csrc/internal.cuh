@@ -147,6 +147,8 @@ struct flinng_index {
     uint64_t device_bytes;
     uint32_t query_mode;   // FLINNG_QUERY_PLAIN, _FUSED or _GRAPH
     uint32_t probes;       // buckets probed per table (0 or 1: the query's own only)
+    cudaStream_t side;     // second stream of the insert's concurrent passes (created on first use)
+    cudaEvent_t ev_fork, ev_join;
     int sms;               // multiprocessors of the device (0: not looked up yet)
     flinng::OccEntry occ[8];          // occupancy of recent fused launch shapes
     uint32_t n_occ;

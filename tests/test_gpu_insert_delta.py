@@ -50,7 +50,7 @@ def sets_slice(pts, lo, hi):
 @pytest.mark.parametrize("W", [4, 7, 14])
 def test_jaccard_insert_sequence(F, W):
     R, B, L, K = 2, 300, 12, 2
-    sizes = [1500, 1, 7, 300, 4096, 5000, 250]          # build, then inserts (5000 * R > 8192: full merge)
+    sizes = [1500, 1, 7, 300, 1500, 4096, 5000, 250]    # build, then inserts (5000 * R > 8192: full merge)
     N = sum(sizes)
     pts = WL.random_sets(70 + W, N, 5000, 20, 200)
     q = WL.random_sets(71 + W, 60, 5000, 20, 200)
