@@ -476,6 +476,20 @@ def serving_runs(F, ix, c: dict, plain_qps: float, factors, check_sample: int = 
     import torch
     keep = []
     k = max(100, c["k"])
+    # the served batches (<= 1,024 queries) run the fused form at shapes tuned
+    # for their size classes, on leading queries of the workload (the class of
+    # the whole batch keeps the shape chosen for it already)
+    def size_class(n):
+        return max(0, int(n - 1).bit_length())
+    for nb in (1024, 256):
+        if size_class(nb) == size_class(c["nq"]):
+            continue
+        if c["metric"] == "cosine":
+            ix.tune(np.ascontiguousarray(c["q"][:nb]), k)
+        else:
+            qoff, qel = c["q"]
+            m = min(nb, len(qoff) - 1)
+            ix.tune((qoff[:m + 1].astype(np.uint64), np.ascontiguousarray(qel[:qoff[m]])), k)
     srv = F.Server(hbm_budget=ix.device_bytes + (2 << 30), n_slots=8, max_batch=1024, k_max=k,
                    max_batch_elems=1 << 21)
     sid = srv.add_index(ix)

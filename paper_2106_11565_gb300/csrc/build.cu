@@ -454,24 +454,56 @@ k_merge_big(const uint32_t *__restrict__ off, const uint16_t *__restrict__ cells
     }
 }
 
-__global__ void k_heavy_flag(const uint32_t *__restrict__ off, uint64_t nslot, uint32_t heavy_min,
-                             uint32_t *__restrict__ flag)
+// One pass over the slots, four per thread (16-byte accesses): hidx[s] = the
+// bitmap row of heavy slot s (a list of at least heavy_min cells) or
+// kEmpty32; the heavy slots appended to list (warp-aggregated; row order is
+// the append order, which no result depends on), their number in *nh.
+__global__ void k_heavy_collect(const uint32_t *__restrict__ off, uint64_t nslot, uint32_t heavy_min,
+                                uint32_t *__restrict__ hidx, uint32_t *__restrict__ list, uint32_t *__restrict__ nh)
 {
-    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nslot;
-         s += uint64_t(gridDim.x) * blockDim.x)
-        flag[s] = (off[s + 1] - off[s]) >= heavy_min ? 1u : 0u;
-}
-
-// hidx[s] = bitmap index of heavy slot s (exclusive prefix of the flags) or
-// kEmpty32; the heavy slots, in slot order, into list.
-__global__ void k_heavy_list(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pre, uint64_t nslot,
-                             uint32_t *__restrict__ hidx, uint32_t *__restrict__ list)
-{
-    for (uint64_t s = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < nslot;
-         s += uint64_t(gridDim.x) * blockDim.x) {
-        const bool heavy = flag[s] != 0u;
-        hidx[s] = heavy ? pre[s] : kEmpty32;
-        if (heavy) list[pre[s]] = uint32_t(s);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t nv = (nslot + 3) / 4;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t v = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; v - lane < nv; v += stride) {
+        const uint64_t s0 = v * 4;
+        uint32_t o[5] = {0u, 0u, 0u, 0u, 0u};
+        if (v < nv) {
+            if (s0 + 4 <= nslot) {
+                const uint4 a = *reinterpret_cast<const uint4 *>(off + s0);
+                o[0] = a.x;
+                o[1] = a.y;
+                o[2] = a.z;
+                o[3] = a.w;
+                o[4] = off[s0 + 4];
+            } else {
+                for (uint32_t t = 0; t < 5; ++t) o[t] = s0 + t <= nslot ? off[s0 + t] : 0u;
+            }
+        }
+        uint32_t h[4];
+#pragma unroll
+        for (uint32_t t = 0; t < 4; ++t) {
+            const bool heavy = v < nv && s0 + t < nslot && o[t + 1] - o[t] >= heavy_min;
+            const uint32_t m = __ballot_sync(0xffffffffu, heavy);
+            uint32_t base = 0;
+            if (m) {
+                const uint32_t lead = __ffs(m) - 1;
+                if (lane == lead) base = atomicAdd(nh, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, lead);
+            }
+            h[t] = kEmpty32;
+            if (heavy) {
+                h[t] = base + __popc(m & ((1u << lane) - 1u));
+                list[h[t]] = uint32_t(s0 + t);
+            }
+        }
+        if (v < nv) {
+            if (s0 + 4 <= nslot) {
+                *reinterpret_cast<uint4 *>(hidx + s0) = make_uint4(h[0], h[1], h[2], h[3]);
+            } else {
+                for (uint32_t t = 0; t < 4; ++t)
+                    if (s0 + t < nslot) hidx[s0 + t] = h[t];
+            }
+        }
     }
 }
 
@@ -500,20 +532,20 @@ __global__ void k_heavy_fill(const uint32_t *__restrict__ off, const uint16_t *_
 }  // namespace
 
 // Cell bitmaps of the heavy slots (those whose list has >= heavy_min cells).
-// Uses the build scratch slot_a / slot_b and a worklist of at least
+// Uses a word of the build scratch slot_a and a worklist of at least
 // n_cells / heavy_min + 1 entries; grows the bitmap array if needed.
 int build_heavy(flinng_index *ix, void *scan_ws, uint32_t *list)
 {
+    (void)scan_ws;
     const cudaStream_t st = ix->stream;
     const uint64_t nslot = ix->nslot;
-    k_heavy_flag<<<thread_blocks(nslot), 256, 0, st>>>(ix->off, nslot, ix->heavy_min, ix->slot_a);
+    uint32_t *count = ix->slot_a;        // build scratch, free at this point
+    FL_CUDA(cudaMemsetAsync(count, 0, sizeof(uint32_t), st));
+    k_heavy_collect<<<thread_blocks((nslot + 3) / 4), 256, 0, st>>>(ix->off, nslot, ix->heavy_min, ix->hidx, list,
+                                                                    count);
     count_launch();
     FL_CUDA(cudaGetLastError());
-    FL_TRY(scan_exclusive(ix->slot_a, ix->slot_b, nslot, scan_ws, st));
-    k_heavy_list<<<thread_blocks(nslot), 256, 0, st>>>(ix->slot_a, ix->slot_b, nslot, ix->hidx, list);
-    count_launch();
-    FL_CUDA(cudaGetLastError());
-    FL_CUDA(cudaMemcpyAsync(ix->h_flag, ix->slot_b + nslot, 4, cudaMemcpyDeviceToHost, st));
+    FL_CUDA(cudaMemcpyAsync(ix->h_flag, count, 4, cudaMemcpyDeviceToHost, st));
     FL_CUDA(cudaStreamSynchronize(st));
     const uint32_t nh = *ix->h_flag;
     if (ix->BRw * 32 < ix->BR || ix->BRw == 0)
