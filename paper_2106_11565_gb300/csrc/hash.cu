@@ -199,6 +199,7 @@ __global__ void k_add_counter(unsigned long long *dst, const unsigned long long 
 // ------------------------------------------------------------------ DOPH
 
 constexpr int kDophWarps = 8;
+constexpr int kDophUnroll = 4;     // element loads in flight per lane
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t z)
 {
@@ -227,11 +228,32 @@ k_doph(const uint64_t *__restrict__ off, const uint32_t *__restrict__ elems,
         for (uint32_t k = lane; k < nbw; k += 32) occ[k] = 0u;
         __syncwarp();
         const uint64_t beg = off[i], end = off[i + 1];
-        for (uint64_t t = beg + lane; t < end; t += 32) {
-            const uint32_t pe = a * elems[t] + b;
-            const uint32_t bin = __umulhi(pe, nb);
-            atomicMin(&val[bin], pe);
-            atomicOr(&occ[bin >> 5], 1u << (bin & 31));
+        // four element loads in flight per lane, then their bins
+        for (uint64_t t0 = beg + lane; t0 < end; t0 += 32 * kDophUnroll) {
+            uint32_t e[kDophUnroll];
+#pragma unroll
+            for (int u = 0; u < kDophUnroll; ++u) {
+                const uint64_t t = t0 + 32u * u;
+                e[u] = t < end ? elems[t] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kDophUnroll; ++u) {
+                if (t0 + 32u * u >= end) break;
+                const uint32_t pe = a * e[u] + b;
+                const uint32_t bin = __umulhi(pe, nb);
+                atomicMin(&val[bin], pe);
+                // a bin is occupied iff its minimum is below the empty marker,
+                // or an element hashes to the marker's value itself (flagged
+                // here; every other occupancy bit is read off val below, with
+                // no atomic per element on the few bitmap words)
+                if (pe == kEmpty32) atomicOr(&occ[bin >> 5], 1u << (bin & 31));
+            }
+        }
+        __syncwarp();
+        for (uint32_t k0 = 0; k0 < nb; k0 += 32) {                 // a ballot per 32 bins
+            const uint32_t k = k0 + lane;
+            const uint32_t bits = __ballot_sync(0xffffffffu, k < nb && val[k] != kEmpty32);
+            if (lane == 0) occ[k0 >> 5] |= bits;
         }
         __syncwarp();
         if (end > beg) {
