@@ -364,7 +364,9 @@ int flinng_export(flinng_index *idx, uint32_t *off, uint16_t *cells,
 
 /* Counters of the last hash call (cosine): projections the first pass (fp32
  * FMA or tensor cores) could not decide, and those that needed the exact
- * accumulator. */
+ * accumulator. A build or insert hashes its points while its permutation or
+ * group checks run, so a call refused by those checks still leaves the
+ * counters of its hash. */
 int flinng_hash_stats(const flinng_index *idx, uint64_t *n_recheck,
                       uint64_t *n_exact);
 

@@ -588,14 +588,9 @@ int check_perm(flinng_index *ix, const uint32_t *perm, uint64_t n, void *ws)
     Carver c(ws, ~size_t(0));
     uint32_t *seen = c.take<uint32_t>(uint64_t(R) * ((n + 31) / 32) + 1);
     FL_CUDA(cudaMemsetAsync(seen, 0, uint64_t(R) * ((n + 31) / 32) * 4 + 4, st));
-    FL_CUDA(cudaMemsetAsync(ix->flag, 0, 4, st));
     k_perm_check<<<thread_blocks(uint64_t(R) * n), 256, 0, st>>>(perm, R, n, seen, ix->flag);
     count_launch();
     FL_CUDA(cudaGetLastError());
-    FL_CUDA(cudaMemcpyAsync(ix->h_flag, ix->flag, 4, cudaMemcpyDeviceToHost, st));
-    FL_CUDA(cudaStreamSynchronize(st));
-    if (*ix->h_flag & 1u) return set_error(FLINNG_ERR_INVALID_ARG, "perm: entry out of range [0, n)");
-    if (*ix->h_flag & 2u) return set_error(FLINNG_ERR_INVALID_ARG, "perm: a row repeats an index");
     return FLINNG_OK;
 }
 
@@ -633,14 +628,22 @@ int check_groups(flinng_index *ix, const uint16_t *groups, uint64_t n)
 {
     const cudaStream_t st = ix->stream;
     if (n == 0) return FLINNG_OK;
-    FL_CUDA(cudaMemsetAsync(ix->flag, 0, 4, st));
     k_check_groups<<<thread_blocks(uint64_t(ix->cfg.R) * n), 256, 0, st>>>(groups, uint64_t(ix->cfg.R) * n,
                                                                          ix->cfg.B, ix->flag);
     count_launch();
     FL_CUDA(cudaGetLastError());
-    FL_CUDA(cudaMemcpyAsync(ix->h_flag, ix->flag, 4, cudaMemcpyDeviceToHost, st));
-    FL_CUDA(cudaStreamSynchronize(st));
-    if (*ix->h_flag & 8u) return set_error(FLINNG_ERR_INVALID_ARG, "groups: a group id is >= B");
+    return FLINNG_OK;
+}
+
+int check_result(flinng_index *ix)
+{
+    FL_CUDA(cudaMemcpyAsync(ix->h_flag, ix->flag, 4, cudaMemcpyDeviceToHost, ix->stream));
+    FL_CUDA(cudaStreamSynchronize(ix->stream));
+    const uint32_t f = *ix->h_flag;
+    if (f & 1u) return set_error(FLINNG_ERR_INVALID_ARG, "perm: entry out of range [0, n)");
+    if (f & 2u) return set_error(FLINNG_ERR_INVALID_ARG, "perm: a row repeats an index");
+    if (f & 8u) return set_error(FLINNG_ERR_INVALID_ARG, "groups: a group id is >= B");
+    if (f & 4u) return set_error(FLINNG_ERR_INVALID_ARG, "build_buckets: a bucket is >= 2^W");
     return FLINNG_OK;
 }
 
@@ -771,14 +774,15 @@ int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *per
     FL_CUDA(cudaGetLastError());
     std::swap(ix->off, ix->slot_b);
     if (have_old) std::swap(ix->cells, ix->cells_tmp);
-    FL_CUDA(cudaMemcpyAsync(ix->h_flag, ix->off + nslot, 4, cudaMemcpyDeviceToHost, st));
-    FL_CUDA(cudaStreamSynchronize(st));
-    ix->n_cells = *ix->h_flag;
-    ix->n_points = N;
+    // the cell total arrives with the heavy-slot count (one wait, in build_heavy)
+    FL_CUDA(cudaMemcpyAsync(ix->h_flag + 1, ix->off + nslot, 4, cudaMemcpyDeviceToHost, st));
     stage2.end();
     TraceRange stage3("heavy bitmaps");
-    FL_TRY(build_heavy(ix, scan_ws, work));
-    return FLINNG_OK;
+    const int rc = build_heavy(ix, scan_ws, work);
+    if (rc != FLINNG_OK) cudaStreamSynchronize(st);    // the lists are in place either way
+    ix->n_cells = ix->h_flag[1];
+    ix->n_points = N;
+    return rc;
 }
 
 }  // namespace flinng

@@ -316,11 +316,14 @@ int insert_common(flinng_index *ix, const flinng_points *pts, uint64_t n, const 
     }
     uint32_t *buckets = c.take<uint32_t>(n * L);
     void *pws = c.take<char>(perm_check_workspace_bytes(R, n));
-    if (groups) FL_TRY(check_groups(ix, dgroups, n));
-    else FL_TRY(check_perm(ix, dperm, n, pws));
     const size_t hb = hash_ws_bytes(ix, n);
     void *hws = c.take<char>(hb);
     void *iws = c.take<char>(insert_workspace_bytes(ix, n, reset));
+    // the device checks of the inputs run ahead of the hash (which writes only
+    // the workspace); one wait for all of them before the index changes
+    FL_CUDA(cudaMemsetAsync(ix->flag, 0, 4, st));
+    if (groups) FL_TRY(check_groups(ix, dgroups, n));
+    else FL_TRY(check_perm(ix, dperm, n, pws));
     if (given_buckets) {
         if (on_device) {
             FL_CUDA(cudaMemcpyAsync(buckets, given_buckets, n * L * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
@@ -328,20 +331,18 @@ int insert_common(flinng_index *ix, const flinng_points *pts, uint64_t n, const 
             FL_CUDA(cudaMemcpyAsync(buckets, given_buckets, n * L * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
         }
         if (n) {
-            FL_CUDA(cudaMemsetAsync(ix->flag, 0, 4, st));
             k_check_buckets<<<1024, 256, 0, st>>>(buckets, n * L, ix->cfg.range_bits, ix->flag);
             count_launch();
             FL_CUDA(cudaGetLastError());
-            FL_CUDA(cudaMemcpyAsync(ix->h_flag, ix->flag, 4, cudaMemcpyDeviceToHost, st));
-            FL_CUDA(cudaStreamSynchronize(st));
-            if (*ix->h_flag & 4u) return set_error(FLINNG_ERR_INVALID_ARG, "build_buckets: a bucket is >= 2^W");
         }
+    } else {
+        FL_TRY(hash_staged(ix, s, n, buckets, nullptr, nullptr, hws, hb));
     }
+    FL_TRY(check_result(ix));
     if (reset) {
         ix->n_points = 0;
         ix->n_cells = 0;
     }
-    if (!given_buckets) FL_TRY(hash_staged(ix, s, n, buckets, nullptr, nullptr, hws, hb));
     FL_TRY(insert_hashed(ix, buckets, dperm, dgroups, n, iws));
     return FLINNG_OK;
 }

@@ -194,10 +194,14 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
 
 // ---- build.cu
 size_t perm_check_workspace_bytes(uint32_t R, uint64_t n);
+// Input checks on the device: each ORs its error bits into ix->flag (zeroed by
+// the caller first) without waiting; check_result waits for them all and
+// turns the bits into an error.
 int check_perm(flinng_index *ix, const uint32_t *perm, uint64_t n, void *ws);
+int check_groups(flinng_index *ix, const uint16_t *groups, uint64_t n);
+int check_result(flinng_index *ix);
 // Workspace of insert_hashed for n new points (reset: a build from scratch).
 size_t insert_workspace_bytes(const flinng_index *ix, uint64_t n, bool reset);
-int check_groups(flinng_index *ix, const uint16_t *groups, uint64_t n);
 int insert_hashed(flinng_index *ix, const uint32_t *buckets, const uint32_t *perm, const uint16_t *groups,
                   uint64_t n, void *ws);
 int build_heavy(flinng_index *ix, void *scan_ws, uint32_t *list);
