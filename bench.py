@@ -469,19 +469,21 @@ SWEEPS = {
 }
 
 
-def serving_runs(F, ix, c: dict, plain_qps: float, factors, check_sample: int = 0) -> dict:
+def serving_runs(F, ix, c: dict, plain_qps: float, factors, check_sample: int = 0, max_batch: int = 1024) -> dict:
     """Poisson traces replayed by the C serving runtime on one resident index
     at ``factors`` x the plain form's device-resident throughput; optionally
     checks ``check_sample`` served results against the same query run alone."""
     import torch
     keep = []
     k = max(100, c["k"])
-    # the served batches (<= 1,024 queries) run the fused form at shapes tuned
-    # for their size classes, on leading queries of the workload (the class of
-    # the whole batch keeps the shape chosen for it already)
+    # the served batches (<= max_batch queries) run the fused form at shapes
+    # tuned for their size classes, on leading queries of the workload (the
+    # class of the whole batch keeps the shape chosen for it already)
     def size_class(n):
         return max(0, int(n - 1).bit_length())
-    for nb in (1024, 256):
+    for nb in sorted({max_batch, 1024, 256}, reverse=True):
+        if nb > max_batch:
+            continue
         if size_class(nb) == size_class(c["nq"]):
             continue
         if c["metric"] == "cosine":
@@ -490,7 +492,7 @@ def serving_runs(F, ix, c: dict, plain_qps: float, factors, check_sample: int = 
             qoff, qel = c["q"]
             m = min(nb, len(qoff) - 1)
             ix.tune((qoff[:m + 1].astype(np.uint64), np.ascontiguousarray(qel[:qoff[m]])), k)
-    srv = F.Server(hbm_budget=ix.device_bytes + (2 << 30), n_slots=8, max_batch=1024, k_max=k,
+    srv = F.Server(hbm_budget=ix.device_bytes + (2 << 30), n_slots=8, max_batch=max_batch, k_max=k,
                    max_batch_elems=1 << 21)
     sid = srv.add_index(ix)
     staging = srv.staging
@@ -523,7 +525,7 @@ def serving_runs(F, ix, c: dict, plain_qps: float, factors, check_sample: int = 
                 ok &= bool(np.array_equal(ids_s[r], rid[0]) and np.array_equal(sc_s[r], rsc[0]))
             same = {"checked": int(len(pick)), "equal": ok}
     srv.close()
-    out = {"form": "continuous batching (C runtime, 8 streams, batches <= 1024, host buffers)",
+    out = {"form": f"continuous batching (C runtime, 8 streams, batches <= {max_batch}, host buffers)",
            "staging": staging,
            "plain_form_qps": plain_qps, "runs": runs,
            "max_qps": max(r["achieved_qps"] for r in runs.values()),
@@ -1428,7 +1430,7 @@ def run_ours(args, c: dict, rank: int, world: int) -> dict | None:
     # ---- serving form on this index: Poisson traces through the C runtime
     serving = None
     if not args.no_serving and world == 1 and not c.get("embed"):
-        serving = serving_runs(F, ix, c, plain_value, (0.25, 0.5, 2.0))
+        serving = serving_runs(F, ix, c, plain_value, (0.25, 0.5, 2.0), max_batch=args.max_batch)
 
     if rank != 0:
         return None
@@ -1825,7 +1827,7 @@ def main():
                     help="streamed embedding workload only: index this many points instead of the config's "
                          "(small profiling cases; the line says so)")
     ap.add_argument("--max-batch", type=int, default=1024,
-                    help="C5: largest batch the serving runtime forms")
+                    help="largest batch the serving runtime forms (C5 and the serving runs of other workloads)")
     ap.add_argument("--configured", action="store_true",
                     help="time the fused form at the parameters the workload's config names instead of the "
                          "serving form at the recall-target parameters (the default where those are known)")
