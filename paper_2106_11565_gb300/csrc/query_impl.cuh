@@ -847,15 +847,7 @@ __device__ void cta_doph(const QArgs &a, const HArgs &h, uint32_t q, uint32_t *q
         const uint32_t pe = h.da * __ldg(h.q_el + t) + h.db;
         const uint32_t bin = __umulhi(pe, nb);
         atomicMin(&val[bin], pe);
-        // occupancy is read off val below, except for an element hashing to
-        // the empty marker's value itself
-        if (pe == kEmpty32) atomicOr(&occ[bin >> 5], 1u << (bin & 31));
-    }
-    __syncthreads();
-    for (uint32_t k0 = tid & ~31u; k0 < nb; k0 += NT) {     // a ballot per 32 bins
-        const uint32_t k = k0 + (tid & 31);
-        const uint32_t bits = __ballot_sync(0xffffffffu, k < nb && val[k] != kEmpty32);
-        if ((tid & 31) == 0) occ[k0 >> 5] |= bits;
+        atomicOr(&occ[bin >> 5], 1u << (bin & 31));
     }
     __syncthreads();
     if (end > beg) {

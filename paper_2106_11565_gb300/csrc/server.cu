@@ -92,12 +92,29 @@ struct GatherDesc {
     uint64_t n;
 };
 
+// A CTA per request; each thread issues all its loads from host memory (up to
+// kGatherUnroll per pass) before storing, so a request of up to
+// kGatherUnroll * blockDim elements costs one round trip over the link.
+constexpr int kGatherUnroll = 4;
+
 __global__ void k_gather_requests(const GatherDesc *__restrict__ desc, uint32_t nb, uint32_t *__restrict__ dst)
 {
     for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
         const GatherDesc g = desc[i];
         const uint32_t *src = reinterpret_cast<const uint32_t *>(g.src);
-        for (uint64_t t = threadIdx.x; t < g.n; t += blockDim.x) dst[g.dst + t] = src[t];
+        for (uint64_t t0 = threadIdx.x; t0 < g.n; t0 += uint64_t(kGatherUnroll) * blockDim.x) {
+            uint32_t v[kGatherUnroll];
+#pragma unroll
+            for (int u = 0; u < kGatherUnroll; ++u) {
+                const uint64_t t = t0 + uint64_t(u) * blockDim.x;
+                v[u] = t < g.n ? src[t] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kGatherUnroll; ++u) {
+                const uint64_t t = t0 + uint64_t(u) * blockDim.x;
+                if (t < g.n) dst[g.dst + t] = v[u];
+            }
+        }
     }
 }
 
