@@ -83,6 +83,7 @@ constexpr int kEpiWarps = 8;                      // two per TMEM lane quarter, 
 constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 constexpr uint64_t kWaitNs = 1000000000ull;       // bounded mbarrier waits: 1 s
 constexpr uint64_t kTcChunkRows = 16384;          // rows split and hashed per launch
+constexpr size_t kRecheckRowBytes = 160 * 1024;   // largest row of x the re-check stages in shared memory
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -567,6 +568,54 @@ __global__ void k_quant_rows(const float *__restrict__ x, uint64_t ld, uint64_t 
 // Compensated fp32 re-check of listed projections: two-product and two-sum
 // per term (one warp per projection), error at most 2^-23 |p| + 2 g(2d)^2 S
 // with S = sum |w x|. Decided bits are set; the rest go to the next list.
+// xr: the entry's row of x (global or shared memory).
+__device__ __forceinline__ void recheck2_entry(const float *xr, const float *__restrict__ Wm, uint32_t d,
+                                               uint32_t L, uint32_t K, float g2, float tiny, unsigned long long ent,
+                                               uint32_t *__restrict__ codes, unsigned long long *__restrict__ out_list,
+                                               unsigned long long *__restrict__ out_count,
+                                               unsigned long long *__restrict__ stats)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t gr = ent_row(ent);
+    const uint32_t gc = ent_col(ent);
+    const float *wr = Wm + uint64_t(gc) * d;
+    float s = 0.f, c = 0.f, sa = 0.f;
+    for (uint32_t t = lane; t < d; t += 32) {
+        const float xv = xr[t], wv = wr[t];
+        const float h = xv * wv;
+        const float l = fmaf(xv, wv, -h);          // exact product error
+        const float sn = s + h;                     // two-sum
+        const float z = sn - s;
+        c += (s - (sn - z)) + (h - z) + l;
+        s = sn;
+        sa = fmaf(fabsf(xv), fabsf(wv), sa);
+    }
+    // combine the lanes: lane 0 adds the 32 (s, c) pairs with two-sums
+    float ts = 0.f, tc = 0.f;
+    for (int k = 0; k < 32; ++k) {
+        const float sk = __shfl_sync(0xffffffffu, s, k);
+        const float ck = __shfl_sync(0xffffffffu, c, k);
+        const float sn = ts + sk;
+        const float z = sn - ts;
+        tc += (ts - (sn - z)) + (sk - z) + ck;
+        ts = sn;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sa = __shfl_sync(0xffffffffu, sa, 0);
+    const float p = ts + tc;
+    const float margin = fmaf(ldexpf(1.f, -23), fabsf(p), fmaf(g2, sa, tiny));
+    if (lane == 0) {
+        if (fabsf(p) > margin) {
+            if (p > 0.f) atomicOr(&codes[gr * L + gc / K], 1u << (gc % K));
+            if ((p > 0.f) != ((ent & kEntSign) != 0)) atomicAdd(&stats[4], 1ull);
+        } else {
+            out_list[atomicAdd(out_count, 1ull)] = ent;
+        }
+        atomicAdd(&stats[3], 1ull);
+    }
+}
+
 __global__ void k_srp_recheck2(const float *__restrict__ X, uint64_t ldx, const float *__restrict__ Wm, uint32_t d,
                                uint32_t L, uint32_t K, float g2, float tiny,
                                const unsigned long long *__restrict__ rlist,
@@ -574,51 +623,59 @@ __global__ void k_srp_recheck2(const float *__restrict__ X, uint64_t ldx, const 
                                unsigned long long *__restrict__ out_list, unsigned long long *__restrict__ out_count,
                                unsigned long long *__restrict__ stats)
 {
-    const int lane = threadIdx.x & 31;
     const unsigned long long nlist = *rcount;
     const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     for (unsigned long long e = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
          e < nlist; e += nwarps) {
         const unsigned long long ent = rlist[e];
-        const uint64_t gr = ent_row(ent);
-        const uint32_t gc = ent_col(ent);
-        const float *xr = X + gr * ldx;
-        const float *wr = Wm + uint64_t(gc) * d;
-        float s = 0.f, c = 0.f, sa = 0.f;
-        for (uint32_t t = lane; t < d; t += 32) {
-            const float xv = xr[t], wv = wr[t];
-            const float h = xv * wv;
-            const float l = fmaf(xv, wv, -h);          // exact product error
-            const float sn = s + h;                     // two-sum
-            const float z = sn - s;
-            c += (s - (sn - z)) + (h - z) + l;
-            s = sn;
-            sa = fmaf(fabsf(xv), fabsf(wv), sa);
-        }
-        // combine the lanes: lane 0 adds the 32 (s, c) pairs with two-sums
-        float ts = 0.f, tc = 0.f;
-        for (int k = 0; k < 32; ++k) {
-            const float sk = __shfl_sync(0xffffffffu, s, k);
-            const float ck = __shfl_sync(0xffffffffu, c, k);
-            const float sn = ts + sk;
-            const float z = sn - ts;
-            tc += (ts - (sn - z)) + (sk - z) + ck;
-            ts = sn;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
-        sa = __shfl_sync(0xffffffffu, sa, 0);
-        const float p = ts + tc;
-        const float margin = fmaf(ldexpf(1.f, -23), fabsf(p), fmaf(g2, sa, tiny));
-        if (lane == 0) {
-            if (fabsf(p) > margin) {
-                if (p > 0.f) atomicOr(&codes[gr * L + gc / K], 1u << (gc % K));
-                if ((p > 0.f) != ((ent & kEntSign) != 0)) atomicAdd(&stats[4], 1ull);
-            } else {
-                out_list[atomicAdd(out_count, 1ull)] = ent;
-            }
-            atomicAdd(&stats[3], 1ull);
-        }
+        recheck2_entry(X + ent_row(ent) * ldx, Wm, d, L, K, g2, tiny, ent, codes, out_list, out_count, stats);
+    }
+}
+
+// The listed projections grouped by row (a counting sort on the row), so that
+// the re-check stages each row of x once in shared memory for all of its
+// entries (the tensor-core epilogue lists a row's projections far apart).
+__global__ void k_rows_hist(const unsigned long long *__restrict__ rlist, const unsigned long long *__restrict__ rcount,
+                            uint32_t *__restrict__ rowcnt)
+{
+    const unsigned long long n = *rcount;
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (unsigned long long)gridDim.x * blockDim.x)
+        atomicAdd(&rowcnt[ent_row(rlist[e])], 1u);
+}
+
+__global__ void k_rows_scatter(const unsigned long long *__restrict__ rlist,
+                               const unsigned long long *__restrict__ rcount, const uint32_t *__restrict__ rowoff,
+                               uint32_t *__restrict__ fill, unsigned long long *__restrict__ sorted)
+{
+    const unsigned long long n = *rcount;
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long ent = rlist[e];
+        const uint64_t r = ent_row(ent);
+        sorted[rowoff[r] + atomicAdd(&fill[r], 1u)] = ent;
+    }
+}
+
+// A CTA per row with listed entries: the row of x in shared memory, a warp per
+// entry; the same arithmetic, in the same order, as k_srp_recheck2.
+__global__ void k_srp_recheck2_rows(const float *__restrict__ X, uint64_t ldx, const float *__restrict__ Wm,
+                                    uint32_t d, uint32_t L, uint32_t K, float g2, float tiny, uint32_t rows,
+                                    const unsigned long long *__restrict__ sorted, const uint32_t *__restrict__ rowoff,
+                                    uint32_t *__restrict__ codes, unsigned long long *__restrict__ out_list,
+                                    unsigned long long *__restrict__ out_count, unsigned long long *__restrict__ stats)
+{
+    extern __shared__ float xs[];
+    const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (uint32_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const uint32_t e0 = rowoff[r], e1 = rowoff[r + 1];
+        if (e0 == e1) continue;                       // uniform over the CTA
+        const float *xg = X + uint64_t(r) * ldx;
+        for (uint32_t t = threadIdx.x; t < d; t += blockDim.x) xs[t] = xg[t];
+        __syncthreads();
+        for (uint32_t e = e0 + warp; e < e1; e += nw)
+            recheck2_entry(xs, Wm, d, L, K, g2, tiny, sorted[e], codes, out_list, out_count, stats);
+        __syncthreads();                              // before the next row overwrites xs
     }
 }
 
@@ -726,7 +783,8 @@ size_t srp_tc_workspace_bytes(const flinng_index *ix, uint64_t n)
 {
     const uint64_t rows = n < kTcChunkRows ? n : kTcChunkRows;
     return carve_bytes<char>(rows * qrow_bytes(ix->cfg.precision, ix->cfg.dim)) + 3 * carve_bytes<float>(rows) +
-           carve_bytes<unsigned long long>(8) + 2 * carve_bytes<unsigned long long>(rows * ix->P + 1) + 4096;
+           carve_bytes<unsigned long long>(8) + 2 * carve_bytes<unsigned long long>(rows * ix->P + 1) +
+           3 * carve_bytes<uint32_t>(rows + 1) + carve_bytes<char>(scan_workspace_bytes(rows + 1)) + 4096;
 }
 
 // Codes of n rows of x (stride ld) on the tensor cores; same contract as srp_hash.
@@ -748,6 +806,13 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
     unsigned long long *cnt = c.take<unsigned long long>(8);
     unsigned long long *list1 = c.take<unsigned long long>(cap * P + 1);
     unsigned long long *list2 = c.take<unsigned long long>(cap * P + 1);
+    uint32_t *rowcnt = c.take<uint32_t>(cap + 1);
+    uint32_t *rowoff = c.take<uint32_t>(cap + 1);
+    uint32_t *fill = c.take<uint32_t>(cap + 1);
+    void *scan_ws = c.take<char>(scan_workspace_bytes(cap + 1));
+    // stage 2 by row when a row of x fits in shared memory
+    const bool rows_staged = size_t(d) * sizeof(float) <= kRecheckRowBytes;
+    if (rows_staged) FL_TRY(ensure_dyn_smem((const void *)k_srp_recheck2_rows, size_t(d) * sizeof(float)));
     FL_CUDA(cudaMemsetAsync(ix->stats, 0, kStats * sizeof(unsigned long long), st));
     if (n == 0) return FLINNG_OK;
     FL_CUDA(cudaMemsetAsync(buckets, 0, n * L * sizeof(uint32_t), st));
@@ -806,11 +871,31 @@ int srp_hash_tc(flinng_index *ix, const float *x, uint64_t ld, uint64_t n, uint3
         else if (prec == FLINNG_PREC_BF16) FL_TRY(launch_tc<kFormBf16>(mx1, mx2, mw1, mw2, a, rows, st));
         else FL_TRY(launch_tc<kFormFp8>(mx1, mx2, mw1, mw2, a, rows, st));
         // stage 2: compensated fp32; stage 3: fp64 / exact
-        k_srp_recheck2<<<152 * 4, 256, 0, st>>>(x + r0 * ld, ld, ix->srp_w, d, L, K, g2, tiny, list1, cnt,
-                                               buckets + r0 * L, list2, cnt + 1, ix->stats);
-        count_launch();
-        FL_CUDA(cudaGetLastError());
-        FL_TRY(srp_recheck_list(ix, x + r0 * ld, ld, list2, cnt + 1, buckets + r0 * L));
+        if (rows_staged) {
+            // the list grouped by row into list2; stage 2 lists what stays undecided in list1
+            FL_CUDA(cudaMemsetAsync(rowcnt, 0, (rows + 1) * sizeof(uint32_t), st));
+            FL_CUDA(cudaMemsetAsync(fill, 0, (rows + 1) * sizeof(uint32_t), st));
+            k_rows_hist<<<152 * 8, 256, 0, st>>>(list1, cnt, rowcnt);
+            count_launch();
+            FL_CUDA(cudaGetLastError());
+            FL_TRY(scan_exclusive(rowcnt, rowoff, rows, scan_ws, st));
+            k_rows_scatter<<<152 * 8, 256, 0, st>>>(list1, cnt, rowoff, fill, list2);
+            count_launch();
+            FL_CUDA(cudaGetLastError());
+            const unsigned grid = unsigned(rows < 152ull * 8 ? rows : 152ull * 8);
+            k_srp_recheck2_rows<<<grid, 256, size_t(d) * sizeof(float), st>>>(
+                x + r0 * ld, ld, ix->srp_w, d, L, K, g2, tiny, uint32_t(rows), list2, rowoff, buckets + r0 * L, list1,
+                cnt + 1, ix->stats);
+            count_launch();
+            FL_CUDA(cudaGetLastError());
+            FL_TRY(srp_recheck_list(ix, x + r0 * ld, ld, list1, cnt + 1, buckets + r0 * L));
+        } else {
+            k_srp_recheck2<<<152 * 4, 256, 0, st>>>(x + r0 * ld, ld, ix->srp_w, d, L, K, g2, tiny, list1, cnt,
+                                                   buckets + r0 * L, list2, cnt + 1, ix->stats);
+            count_launch();
+            FL_CUDA(cudaGetLastError());
+            FL_TRY(srp_recheck_list(ix, x + r0 * ld, ld, list2, cnt + 1, buckets + r0 * L));
+        }
         FL_TRY(add_counter(ix->stats, cnt, st));            // undecided after the tensor-core pass
     }
     // no synchronisation here (servers hash on their own streams): the flag
