@@ -22,7 +22,7 @@ namespace {
 
 // ------------------------------------------------------------------ SRP
 
-constexpr int kBM = 64, kBN = 64, kBK = 16, kSrpThreads = 256;
+constexpr int kBM = 128, kBN = 64, kBK = 16, kSrpThreads = 256;   // 8 x 4 outputs per thread
 constexpr int kSrpChunkRows = 1 << 14;
 
 __global__ void __launch_bounds__(kSrpThreads)
@@ -32,37 +32,44 @@ k_srp_fp32(const float *__restrict__ X, uint64_t ldx, uint64_t n,
            float *__restrict__ proj, unsigned long long *__restrict__ rlist,
            unsigned long long *__restrict__ rcount)
 {
-    __shared__ float As[kBK][kBM + 4];
-    __shared__ float Bs[kBK][kBN + 4];
+    __shared__ __align__(16) float As[kBK][kBM + 4];
+    __shared__ __align__(16) float Bs[kBK][kBN + 4];
     const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     const uint64_t row0 = uint64_t(blockIdx.x) * kBM;
     const uint32_t col0 = blockIdx.y * kBN;
-    float p[4][4], s[4][4];
+    float p[8][4], s[8][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) p[i][j] = s[i][j] = 0.f;
 
     for (uint32_t k0 = 0; k0 < d; k0 += kBK) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < (kBM * kBK) / kSrpThreads; ++e) {
             const int idx = tid + e * kSrpThreads;
             const int r = idx / kBK, kk = idx % kBK;
             const uint64_t gr = row0 + r;
-            const uint32_t gc = col0 + r, gk = k0 + kk;
+            const uint32_t gk = k0 + kk;
             As[kk][r] = (gr < n && gk < d) ? X[gr * ldx + gk] : 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < (kBN * kBK) / kSrpThreads; ++e) {
+            const int idx = tid + e * kSrpThreads;
+            const int r = idx / kBK, kk = idx % kBK;
+            const uint32_t gc = col0 + r, gk = k0 + kk;
             Bs[kk][r] = (gc < P && gk < d) ? Wm[uint64_t(gc) * d + gk] : 0.f;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kBK; ++kk) {
-            float a[4], b[4];
+            // k in order for every output, as before: the sums are the same
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][ty * 8 + 4]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     p[i][j] = fmaf(a[i], b[j], p[i][j]);
@@ -72,8 +79,8 @@ k_srp_fp32(const float *__restrict__ X, uint64_t ldx, uint64_t n,
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const uint64_t gr = row0 + ty * 4 + i;
+    for (int i = 0; i < 8; ++i) {
+        const uint64_t gr = row0 + ty * 8 + i;
         if (gr >= n) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
