@@ -1086,7 +1086,12 @@ def run_headline(args, c: dict, rank: int, world: int) -> dict | None:
 
     # ---- serving form: continuous batching (C runtime), requests and results in host memory
     keep = []
-    srv = F.Server(hbm_budget=ix.device_bytes + (2 << 30), n_slots=8, max_batch=1024, k_max=k,
+    # batch classes above the tuned one take its launch shape
+    cls = 2048
+    while cls <= args.max_batch and tuning["threads"]:
+        ix.set_tuning(cls, tuning["threads"], tuning["ctas_per_sm"], tuning["cap"])
+        cls *= 2
+    srv = F.Server(hbm_budget=ix.device_bytes + (2 << 30), n_slots=8, max_batch=args.max_batch, k_max=k,
                    max_batch_elems=1 << 21)
     sid = srv.add_index(ix)
     ix.set_query_mode(F.QUERY_FUSED)
@@ -1201,7 +1206,7 @@ def run_headline(args, c: dict, rank: int, world: int) -> dict | None:
         "scaling": "weak", "vs_baseline": None, "dtype": "u32" if ct["metric"] != "cosine" else "f32",
         "data": "synthetic (seeded; stands in for the paper's datasets)",
         "config": headline_config(args.workload, ct, world),
-        "form": "serving: continuous batching over 8 CUDA streams (C runtime), batches <= 1024 queries, "
+        "form": f"serving: continuous batching over 8 CUDA streams (C runtime), batches <= {args.max_batch} queries, "
                 "request sets read from host memory by a gather kernel, results copied to the caller's host "
                 "buffers; value = queries / device time (CUDA events, first copy in .. last result out)",
         "recall": rec, "recall_target_met": rec["recall_at_10"] >= 0.9,
